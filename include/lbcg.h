@@ -1,0 +1,219 @@
+/*
+ * lbcg.h -- C ABI of the GB300 (sm_103a) library for the regularized
+ * colour-gradient lattice Boltzmann method for two immiscible components
+ * (Montessori, Lauricella, La Rocca, Succi, Stolovicki, Ziblat, Weitz,
+ * arXiv:1711.02003).
+ *
+ * The library advances the populations f_i^k (k = red, blue) of Eq. 1 with the
+ * fused per-site update:
+ *   streaming (Eq. 1) with halfway bounce-back walls and ghost-site ports,
+ *   densities rho^k and momentum (Eqs. 2-3), the phase field
+ *   psi = (rho_R - rho_B)/rho and its isotropic gradient F (Sec. II, colour
+ *   gradient), relaxation at the mixture relaxation time regularized by the
+ *   second-order Hermite projection (Eqs. 5, 6, 11), the surface-tension
+ *   perturbation with parameter A (Eq. 9) and recolouring with beta (Eq. 10).
+ * The composition of Eq. 4 is applied as relax -> perturb -> recolour on the
+ * total f = f^R + f^B; only recolouring separates the components.
+ *
+ * Conventions for every entry point:
+ *   - Return LBCG_OK (0) on success or a negative LBCG_ERR_* code; nothing is
+ *     thrown across the ABI.  lbcg_last_error() gives a message for the calling
+ *     thread's last failure.
+ *   - All GPU work is enqueued on the CUDA stream given to lbcg_create (NULL is
+ *     the legacy default stream).  Calls taking HOST pointers copy synchronously
+ *     and return after the copy; calls taking DEVICE pointers are asynchronous
+ *     on that stream.
+ *   - The library allocates only small device tables (per-site link flags,
+ *     port ghost lists, reduction partials) at lbcg_set_geometry.  The two
+ *     population buffers are owned by the caller (e.g. torch tensors) and bound
+ *     with lbcg_bind_state; between steps the inactive buffer is used as scratch
+ *     by read-back, labelling and initialisation calls.
+ *   - Per-site arrays are indexed site = x + nx*(y + ny*z), x fastest.
+ *   - Population layout seen through lbcg_get_populations/lbcg_set_populations:
+ *     FP64 [k][i][site], k = 0 red, 1 blue, directions 0-based with 0 = rest:
+ *       D2Q9 : (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+ *       D3Q19: (0,0,0) (1,0,0) (-1,0,0) (0,1,0) (0,-1,0) (0,0,1) (0,0,-1)
+ *              (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1)
+ *              (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+ *     The stored state is post-collision (what Eq. 1 streams next).
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef LBCG_H
+#define LBCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBCG_ABI_VERSION 1
+#define LBCG_MAX_PORTS 8
+
+enum lbcg_status {
+    LBCG_OK = 0,
+    LBCG_ERR_ARG = -1,       /* invalid argument: null pointer, size, parameter out of range */
+    LBCG_ERR_STATE = -2,     /* call out of order: no state bound, no geometry, no fields */
+    LBCG_ERR_CUDA = -3,      /* CUDA runtime failure (message in lbcg_last_error) */
+    LBCG_ERR_NOMEM = -4,     /* a library-internal device allocation failed */
+    LBCG_ERR_DIVERGED = -5,  /* non-finite or non-positive density found */
+    LBCG_ERR_GEOMETRY = -6,  /* invalid mask / port table */
+    LBCG_ERR_CAPACITY = -7,  /* caller buffer too small */
+    LBCG_ERR_UNSUPPORTED = -8
+};
+
+enum lbcg_lattice { LBCG_D2Q9 = 0, LBCG_D3Q19 = 1 };
+
+/* Storage precision of the populations.  Arithmetic is FP64 for LBCG_FP64 and
+ * FP32 for the others.
+ *   LBCG_FP64        f^R_i, f^B_i in double
+ *   LBCG_FP32        f^R_i, f^B_i in float
+ *   LBCG_FP32_DEV    red f^R_i and total deviation g_i = f^R_i + f^B_i - w_i rho0 in float
+ *   LBCG_FP16_SCALED red deviation and total deviation in binary16 with fixed scale factors */
+enum lbcg_precision { LBCG_FP64 = 0, LBCG_FP32 = 1, LBCG_FP32_DEV = 2, LBCG_FP16_SCALED = 3 };
+
+/* Eq. 11 regularized relaxation, or the plain BGK relaxation of Eq. 5 */
+enum lbcg_collision { LBCG_REG = 0, LBCG_BGK = 1 };
+
+/* Mask codes: fluid, wall (halfway bounce-back), or a ghost site of port m (code 2 + m). */
+enum lbcg_mask { LBCG_MASK_FLUID = 0, LBCG_MASK_WALL = 1, LBCG_MASK_PORT0 = 2 };
+
+/* Port kinds.  Ghost sites are refilled before each streaming step from their inward
+ * neighbour x' = ghost + normal:
+ *   VELOCITY       f^k = f^{k,eq}(chi^k rho(x'), u_port) + chi^k (f(x') - f^eq(x')),
+ *                  chi^R = (1+psi)/2, chi^B = (1-psi)/2 of the port's colour psi;
+ *   PRESSURE       f^k = f^{k,eq}(rho_port rho^k(x')/rho(x'), u(x')) + f^k(x') - f^{k,eq}(x');
+ *   ZERO_GRADIENT  f^k = f^k(x').
+ * The paper prints no boundary rule; these are the library's definitions. */
+enum lbcg_port_kind { LBCG_PORT_VELOCITY = 0, LBCG_PORT_PRESSURE = 1, LBCG_PORT_ZERO_GRADIENT = 2 };
+/* Velocity profile over the port's bounding box in the transverse axes; the walls sit
+ * halfway beyond the first and last port sites: u = u_max * prod 4 s (W - s) / W^2. */
+enum lbcg_profile { LBCG_PROFILE_PARABOLIC = 0, LBCG_PROFILE_FLAT = 1 };
+
+typedef struct {
+    int lattice;        /* lbcg_lattice */
+    int nx, ny, nz;     /* box; nz is ignored (1) for D2Q9 */
+    int periodic[3];    /* per axis; a closed axis acts as a wall outside the box */
+    int collision;      /* lbcg_collision */
+    int precision;      /* lbcg_precision */
+    double tau_r, tau_b;     /* relaxation times of red and blue, > 1/2 (Eq. 5) */
+    double alpha_r, alpha_b; /* Eq. 7 free parameters in (0,1); alpha = w_0 gives density ratio 1 */
+    double A;           /* surface-tension parameter of Eq. 9, >= 0 */
+    double beta;        /* recolouring parameter of Eq. 10, in [0,1] */
+    double rho0;        /* reference density of the deviation storage (and default port density) */
+    double psi_wall;    /* phase field seen at wall sites by the colour gradient, in [-1,1] */
+} lbcg_params;
+
+typedef struct {
+    int kind;           /* lbcg_port_kind */
+    int normal_axis;    /* 0,1,2: axis of the inward normal */
+    int normal_sign;    /* +1 or -1 */
+    int profile;        /* lbcg_profile (velocity ports) */
+    double u_max;       /* peak inflow speed along the inward normal (velocity ports) */
+    double rho;         /* imposed density (pressure ports) */
+    double psi;         /* colour of the injected fluid, +1 red .. -1 blue (velocity ports) */
+} lbcg_port;
+
+/* Observables of the stored state over fluid sites (FP64 reductions on the GPU):
+ * component masses (Eq. 2), momentum (Eq. 3), pressure p = sum_k c_p(alpha_k) rho^k
+ * (Eq. 8: c_p = 3(1-alpha)/5 in D2Q9; (1-alpha)/2 in D3Q19) averaged inside r < r_in
+ * and outside r > r_out of a centre (minimum-image distance on periodic axes), their
+ * difference dp (Laplace pressure), the equivalent radius from the red amount
+ * sum (1+psi)/2, and max |u| (spurious currents). */
+typedef struct {
+    double mass_r, mass_b;
+    double mom[3];
+    double p_in, p_out, dp;
+    double r_eff;
+    double umax;
+    double amount;      /* sum over fluid sites of (1+psi)/2 */
+    double n_in, n_out; /* sites in the two pressure windows */
+    long long step;
+    int nonfinite;      /* fluid sites with non-finite or non-positive density */
+    int pad_;
+} lbcg_obs;
+
+typedef struct lbcg_ctx lbcg_ctx;
+
+/* Human-readable name of a status code (static string). */
+const char* lbcg_strerror(int status);
+/* Message of the calling thread's last failed call (static per thread, never NULL). */
+const char* lbcg_last_error(void);
+/* LBCG_ABI_VERSION of the loaded library. */
+int lbcg_abi_version(void);
+
+/* Bytes of ONE population buffer for these parameters (0 if they are invalid).
+ * Layout: 2*Q planes of npad values of the storage type, npad = nsites rounded up to
+ * a multiple of 128, each plane 256-byte aligned relative to the buffer start. */
+size_t lbcg_state_bytes(const lbcg_params* p);
+
+/* Validate parameters and create a context on the current CUDA device.
+ * stream: a cudaStream_t (NULL = legacy default stream) on which all work runs.
+ * Errors: LBCG_ERR_ARG for an invalid parameter (tau <= 1/2, beta outside [0,1],
+ * A < 0, alpha outside (0,1), non-positive size, unknown lattice/precision). */
+int lbcg_create(const lbcg_params* p, void* stream, lbcg_ctx** out);
+void lbcg_destroy(lbcg_ctx* ctx);
+
+/* Bind caller-owned device buffers (each >= lbcg_state_bytes, 256-byte aligned).
+ * The library never frees them; they must outlive the context's use of them. */
+int lbcg_bind_state(lbcg_ctx* ctx, void* dev_a, void* dev_b, size_t bytes_each);
+
+/* Geometry: host mask of nsites codes (lbcg_mask) and the port table.  Every port
+ * ghost's inward neighbour must be a fluid site, and every port index used by the
+ * mask must be < nports (else LBCG_ERR_GEOMETRY).  Allocates the library's device
+ * tables (replacing earlier ones).  Synchronous. */
+int lbcg_set_geometry(lbcg_ctx* ctx, const uint8_t* host_mask, const lbcg_port* ports, int nports);
+
+/* Initial state f^k = f^{k,eq}(rho^k, u) (Eq. 6) on fluid sites, zero elsewhere.
+ * rho_r, rho_b: nsites doubles; u: dim*nsites doubles ([axis][site]) or NULL (rest).
+ * Host pointers (synchronous) or device pointers (_device, asynchronous). Resets the step counter. */
+int lbcg_init_fields(lbcg_ctx* ctx, const double* rho_r, const double* rho_b, const double* u);
+int lbcg_init_fields_device(lbcg_ctx* ctx, const double* rho_r, const double* rho_b, const double* u);
+
+/* Advance n >= 0 steps, asynchronously on the context's stream. */
+int lbcg_step(lbcg_ctx* ctx, long long n);
+long long lbcg_step_count(const lbcg_ctx* ctx);
+int lbcg_synchronize(lbcg_ctx* ctx);
+
+/* Macroscopic fields of the stored state (Eqs. 2-3): rho_r, rho_b (nsites) and
+ * u (dim*nsites, [axis][site]); zeros at non-fluid sites.  Host (synchronous) or
+ * device (asynchronous) destinations. */
+int lbcg_get_fields(lbcg_ctx* ctx, double* rho_r, double* rho_b, double* u);
+int lbcg_get_fields_device(lbcg_ctx* ctx, double* rho_r, double* rho_b, double* u);
+
+/* Populations of the stored state as FP64 f^k_i in the layout above (2*Q*nsites
+ * doubles, host), converted from the storage precision; and the reverse. */
+int lbcg_get_populations(lbcg_ctx* ctx, double* host_f);
+int lbcg_set_populations(lbcg_ctx* ctx, const double* host_f);
+
+/* Observables (see lbcg_obs).  centre[3] in lattice units; r_in < 0 selects
+ * r_eff/2 and r_out < 0 selects r_eff + 5 (the paper's interface width of about
+ * 5 lattice units, Sec. III).  Synchronous.  Returns LBCG_ERR_DIVERGED (with *out
+ * filled) when nonfinite > 0. */
+int lbcg_observables(lbcg_ctx* ctx, const double centre[3], double r_in, double r_out, lbcg_obs* out);
+
+/* Droplet labelling: connected components of {fluid sites with rho_R > rho_B}
+ * (psi > 0), face-connected, wrapping periodic axes.  labels[nsites] receives the
+ * smallest linear site index of the site's component, or -1.  counts/volumes (may be
+ * NULL) receive, in increasing label order, each droplet's site count and its
+ * sum of (1+psi)/2, for at most cap droplets; *n_drops receives the total number.
+ * Synchronous. */
+int lbcg_label(lbcg_ctx* ctx, int32_t* labels, int64_t* counts, double* volumes, int cap, int* n_drops);
+
+/* Kernel timing: when enabled, CUDA events bracket every launch of the fused step
+ * kernel on the context's stream; lbcg_kernel_time returns the summed duration in
+ * milliseconds and the number of launches since the last reset (synchronises). */
+int lbcg_set_kernel_timing(lbcg_ctx* ctx, int enable);
+int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
+
+/* Launch shape of the fused step kernel (0 = library default):
+ * rows: sites per warp along the marching axis (D2Q9: y rows per warp strip;
+ * D3Q19: z planes per block); block_rows: D3Q19 warps per block along y (>= 3). */
+int lbcg_set_launch(lbcg_ctx* ctx, int rows, int block_rows);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBCG_H */

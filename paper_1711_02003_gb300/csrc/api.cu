@@ -1,0 +1,685 @@
+// api.cu -- host side of the C ABI declared in include/lbcg.h: parameter checks,
+// geometry preprocessing (link words, port ghost tables, inlet profiles), buffer
+// binding, step sequencing and synchronous read-back.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lbcg_device.cuh"
+
+using namespace lbcg;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where)
+{
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return LBCG_ERR_CUDA;
+}
+
+#define LBCG_CUDA(call, where)                          \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+int q_of(int lattice) { return lattice == LBCG_D2Q9 ? 9 : 19; }
+
+long long sites_of(const lbcg_params* p)
+{
+    return (long long)p->nx * p->ny * (p->lattice == LBCG_D2Q9 ? 1 : p->nz);
+}
+
+int validate(const lbcg_params* p)
+{
+    if (!p) return fail(LBCG_ERR_ARG, "null parameters");
+    if (p->lattice != LBCG_D2Q9 && p->lattice != LBCG_D3Q19) return fail(LBCG_ERR_ARG, "unknown lattice");
+    if (p->precision < LBCG_FP64 || p->precision > LBCG_FP16_SCALED) return fail(LBCG_ERR_ARG, "unknown precision");
+    if (p->collision != LBCG_REG && p->collision != LBCG_BGK) return fail(LBCG_ERR_ARG, "unknown collision");
+    if (p->nx < 1 || p->ny < 1 || (p->lattice == LBCG_D3Q19 && p->nz < 1))
+        return fail(LBCG_ERR_ARG, "box sizes must be >= 1");
+    const long long n = sites_of(p);
+    if (n > (long long)INT32_MAX - 1) return fail(LBCG_ERR_ARG, "more than 2^31-2 sites");
+    if (!(p->tau_r > 0.5) || !(p->tau_b > 0.5)) return fail(LBCG_ERR_ARG, "relaxation times must exceed 1/2");
+    if (!(p->beta >= 0.0 && p->beta <= 1.0)) return fail(LBCG_ERR_ARG, "beta must lie in [0,1]");
+    if (!(p->A >= 0.0) || !std::isfinite(p->A)) return fail(LBCG_ERR_ARG, "A must be finite and >= 0");
+    if (!(p->alpha_r > 0.0 && p->alpha_r < 1.0) || !(p->alpha_b > 0.0 && p->alpha_b < 1.0))
+        return fail(LBCG_ERR_ARG, "alpha_k must lie in (0,1)");
+    if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) return fail(LBCG_ERR_ARG, "rho0 must be > 0");
+    if (!(p->psi_wall >= -1.0 && p->psi_wall <= 1.0)) return fail(LBCG_ERR_ARG, "psi_wall must lie in [-1,1]");
+    return LBCG_OK;
+}
+
+size_t elem_size(int precision)
+{
+    switch (precision) {
+        case LBCG_FP64: return 8;
+        case LBCG_FP32:
+        case LBCG_FP32_DEV: return 4;
+        default: return 2;
+    }
+}
+
+size_t padded(long long n) { return (size_t)((n + 127) / 128 * 128); }
+
+// lattice velocity sets in the ABI order, for host-side geometry work
+void host_c(int lattice, int i, int c[3])
+{
+    if (lattice == LBCG_D2Q9) {
+        c[0] = Lat<0>::cx(i);
+        c[1] = Lat<0>::cy(i);
+        c[2] = 0;
+    } else {
+        c[0] = Lat<1>::cx(i);
+        c[1] = Lat<1>::cy(i);
+        c[2] = Lat<1>::cz(i);
+    }
+}
+
+template <typename T>
+void fill_phys(Phys<T>& ph, const lbcg_params& p, int lattice)
+{
+    const double nu_r = (p.tau_r - 0.5) / 3.0, nu_b = (p.tau_b - 0.5) / 3.0;
+    const double w[3] = {lattice == 0 ? 4.0 / 9.0 : 1.0 / 3.0, lattice == 0 ? 1.0 / 9.0 : 1.0 / 18.0, 1.0 / 36.0};
+    // Eq. 7 for D2Q9; D3Q19 uses alpha, (1-alpha)/12, (1-alpha)/24 (reduces to w_i at alpha = 1/3)
+    const double d1 = lattice == 0 ? 5.0 : 12.0, d2 = lattice == 0 ? 20.0 : 24.0;
+    const double phR[3] = {p.alpha_r, (1.0 - p.alpha_r) / d1, (1.0 - p.alpha_r) / d2};
+    const double phB[3] = {p.alpha_b, (1.0 - p.alpha_b) / d1, (1.0 - p.alpha_b) / d2};
+    ph.rho0 = (T)p.rho0;
+    ph.half_inv_nu_r = (T)(0.5 / nu_r);
+    ph.half_inv_nu_b = (T)(0.5 / nu_b);
+    ph.A = (T)p.A;
+    ph.beta = (T)p.beta;
+    ph.psi_wall = (T)p.psi_wall;
+    for (int c = 0; c < 3; ++c) {
+        ph.phiR[c] = (T)phR[c];
+        ph.phiB[c] = (T)phB[c];
+        ph.dphiR[c] = (T)(phR[c] - w[c]);
+        ph.dphiB[c] = (T)(phB[c] - w[c]);
+        ph.wr0[c] = (T)(w[c] * p.rho0);
+    }
+    ph.scale_g = (T)256.0;
+    ph.inv_scale_g = (T)(1.0 / 256.0);
+}
+
+}  // namespace
+
+namespace lbcg {
+
+size_t storage_size(int precision) { return elem_size(precision); }
+
+void fill_kparams(lbcg_ctx* c)
+{
+    KParams& k = c->kp;
+    std::memset(&k, 0, sizeof(k));
+    k.nx = c->dims[0];
+    k.ny = c->dims[1];
+    k.nz = c->dims[2];
+    for (int a = 0; a < 3; ++a) k.per[a] = c->p.periodic[a] ? 1 : 0;
+    if (c->p.lattice == LBCG_D2Q9) k.per[2] = 1;
+    k.np = c->np;
+    k.collision = c->p.collision;
+    k.lattice = c->p.lattice;
+    k.alpha_r = c->p.alpha_r;
+    k.alpha_b = c->p.alpha_b;
+    fill_phys(k.pf, c->p, c->p.lattice);
+    fill_phys(k.pd, c->p, c->p.lattice);
+    const int sms = 152;
+    if (c->p.lattice == LBCG_D2Q9) {
+        k.nsx = (k.nx + 29) / 30;
+        int rows = c->rows;
+        if (rows <= 0) {
+            const long long target = (long long)sms * 24 * 3;  // about three waves of warps
+            long long r = ((long long)k.nsx * k.ny) / target;
+            rows = (int)std::max(4LL, std::min(64LL, r));
+        }
+        k.rows = std::min(rows, k.ny);
+        k.nsy = (k.ny + k.rows - 1) / k.rows;
+        k.nsz = 1;
+    } else {
+        const int wy = c->block_rows > 2 ? c->block_rows : 16;
+        c->block_rows = wy;
+        k.nsx = (k.nx + 29) / 30;
+        k.nsy = (k.ny + (wy - 2) - 1) / (wy - 2);
+        int rows = c->rows;
+        if (rows <= 0) {
+            const long long per_slab = (long long)k.nsx * k.nsy;
+            const long long want = (long long)sms * 3;
+            long long nsz = (want + per_slab - 1) / per_slab;
+            rows = (int)std::max(4LL, std::min(64LL, (k.nz + nsz - 1) / std::max(1LL, nsz)));
+        }
+        k.rows = std::min(rows, k.nz);
+        k.nsz = (k.nz + k.rows - 1) / k.rows;
+    }
+}
+
+}  // namespace lbcg
+
+static void free_tables(lbcg_ctx* c)
+{
+    cudaFree(c->d_link);
+    cudaFree(c->d_ghost);
+    cudaFree(c->d_ghost_u);
+    c->d_link = nullptr;
+    c->d_ghost = nullptr;
+    c->d_ghost_u = nullptr;
+}
+
+extern "C" {
+
+const char* lbcg_strerror(int s)
+{
+    switch (s) {
+        case LBCG_OK: return "ok";
+        case LBCG_ERR_ARG: return "invalid argument";
+        case LBCG_ERR_STATE: return "call out of order";
+        case LBCG_ERR_CUDA: return "CUDA error";
+        case LBCG_ERR_NOMEM: return "out of device memory";
+        case LBCG_ERR_DIVERGED: return "non-finite or non-positive density";
+        case LBCG_ERR_GEOMETRY: return "invalid geometry";
+        case LBCG_ERR_CAPACITY: return "output capacity too small";
+        case LBCG_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+const char* lbcg_last_error(void) { return g_err.c_str(); }
+
+int lbcg_abi_version(void) { return LBCG_ABI_VERSION; }
+
+size_t lbcg_state_bytes(const lbcg_params* p)
+{
+    if (validate(p) != LBCG_OK) return 0;
+    return (size_t)2 * q_of(p->lattice) * padded(sites_of(p)) * elem_size(p->precision);
+}
+
+int lbcg_create(const lbcg_params* p, void* stream, lbcg_ctx** out)
+{
+    if (!out) return fail(LBCG_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    int st = validate(p);
+    if (st) return st;
+    lbcg_ctx* c = new (std::nothrow) lbcg_ctx();
+    if (!c) return fail(LBCG_ERR_NOMEM, "host allocation failed");
+    c->p = *p;
+    if (c->p.lattice == LBCG_D2Q9) c->p.nz = 1;
+    c->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    c->Q = q_of(c->p.lattice);
+    c->D = c->p.lattice == LBCG_D2Q9 ? 2 : 3;
+    c->dims[0] = c->p.nx;
+    c->dims[1] = c->p.ny;
+    c->dims[2] = c->p.nz;
+    c->n = sites_of(&c->p);
+    c->np = padded(c->n);
+    c->state_bytes = (size_t)2 * c->Q * c->np * elem_size(c->p.precision);
+    fill_kparams(c);
+    *out = c;
+    return LBCG_OK;
+}
+
+void lbcg_destroy(lbcg_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_tables(c);
+    cudaFree(c->d_partials);
+    cudaFree(c->d_result);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+int lbcg_bind_state(lbcg_ctx* c, void* a, void* b, size_t bytes)
+{
+    if (!c || !a || !b) return fail(LBCG_ERR_ARG, "null context or buffer");
+    if (a == b) return fail(LBCG_ERR_ARG, "the two state buffers must differ");
+    if (bytes < c->state_bytes) return fail(LBCG_ERR_ARG, "state buffers smaller than lbcg_state_bytes");
+    if (((uintptr_t)a | (uintptr_t)b) & 255u) return fail(LBCG_ERR_ARG, "state buffers must be 256-byte aligned");
+    c->A = a;
+    c->B = b;
+    c->bound = true;
+    c->fields = false;
+    return LBCG_OK;
+}
+
+int lbcg_set_geometry(lbcg_ctx* c, const uint8_t* mask, const lbcg_port* ports, int nports)
+{
+    if (!c || !mask) return fail(LBCG_ERR_ARG, "null context or mask");
+    if (nports < 0 || nports > LBCG_MAX_PORTS || (nports > 0 && !ports))
+        return fail(LBCG_ERR_ARG, "port count out of range");
+    const int nx = c->dims[0], ny = c->dims[1], nz = c->dims[2];
+    const long long n = c->n;
+    const int Q = c->Q;
+    int per[3] = {c->p.periodic[0] ? 1 : 0, c->p.periodic[1] ? 1 : 0, c->p.periodic[2] ? 1 : 0};
+    if (c->p.lattice == LBCG_D2Q9) per[2] = 1;
+    for (int m = 0; m < nports; ++m) {
+        const lbcg_port& pt = ports[m];
+        if (pt.kind < 0 || pt.kind > 2) return fail(LBCG_ERR_GEOMETRY, "unknown port kind");
+        if (pt.normal_axis < 0 || pt.normal_axis >= c->D || (pt.normal_sign != 1 && pt.normal_sign != -1))
+            return fail(LBCG_ERR_GEOMETRY, "bad port normal");
+        if (!(pt.psi >= -1.0 && pt.psi <= 1.0) || !(pt.rho > 0.0) || !std::isfinite(pt.u_max))
+            return fail(LBCG_ERR_GEOMETRY, "bad port values");
+    }
+    std::vector<uint32_t> link((size_t)n);
+    bool any = false;
+    long long fluid = 0;
+    int lo[LBCG_MAX_PORTS][3], hi[LBCG_MAX_PORTS][3];
+    for (int m = 0; m < LBCG_MAX_PORTS; ++m)
+        for (int a = 0; a < 3; ++a) {
+            lo[m][a] = 1 << 30;
+            hi[m][a] = -1;
+        }
+    std::vector<long long> ghosts;
+    auto at = [&](long long x, long long y, long long z) { return x + (long long)nx * (y + (long long)ny * z); };
+    for (long long s = 0; s < n; ++s) {
+        const int code = mask[s];
+        const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
+        if (code == LBCG_MASK_WALL) {
+            link[s] = kTypeWall << kTypeShift;
+            any = true;
+            continue;
+        }
+        if (code >= LBCG_MASK_PORT0) {
+            const int m = code - LBCG_MASK_PORT0;
+            if (m >= nports) return fail(LBCG_ERR_GEOMETRY, "mask names a port beyond nports");
+            link[s] = kTypePort << kTypeShift;
+            any = true;
+            int v[3] = {x, y, z};
+            for (int a = 0; a < 3; ++a) {
+                lo[m][a] = std::min(lo[m][a], v[a]);
+                hi[m][a] = std::max(hi[m][a], v[a]);
+            }
+            v[ports[m].normal_axis] += ports[m].normal_sign;
+            const int dims[3] = {nx, ny, nz};
+            const int ax = ports[m].normal_axis;
+            if (v[ax] < 0 || v[ax] >= dims[ax] || mask[at(v[0], v[1], v[2])] != LBCG_MASK_FLUID)
+                return fail(LBCG_ERR_GEOMETRY, "a port ghost's inward neighbour is not a fluid site");
+            ghosts.push_back(s);
+            continue;
+        }
+        if (code != LBCG_MASK_FLUID) return fail(LBCG_ERR_GEOMETRY, "unknown mask code");
+        ++fluid;
+        uint32_t lk = 0;
+        for (int i = 1; i < Q; ++i) {
+            int cc[3];
+            host_c(c->p.lattice, i, cc);
+            int v[3] = {x - cc[0], y - cc[1], z - cc[2]};
+            const int dims[3] = {nx, ny, nz};
+            bool out = false;
+            for (int a = 0; a < 3; ++a) {
+                if (v[a] < 0 || v[a] >= dims[a]) {
+                    if (!per[a]) out = true;
+                    v[a] = (v[a] + dims[a]) % dims[a];
+                }
+            }
+            if (out || mask[at(v[0], v[1], v[2])] == LBCG_MASK_WALL) lk |= 1u << i;
+        }
+        if (lk) any = true;
+        link[s] = lk;
+    }
+    // ghost table: [site | inward neighbour | port | kind] and [ux | uy | uz | rho | psi]
+    const int ng = (int)ghosts.size();
+    std::vector<int> tab((size_t)4 * std::max(ng, 1));
+    std::vector<double> gu((size_t)5 * std::max(ng, 1));
+    for (int t = 0; t < ng; ++t) {
+        const long long s = ghosts[t];
+        const int m = mask[s] - LBCG_MASK_PORT0;
+        const lbcg_port& pt = ports[m];
+        int v[3] = {(int)(s % nx), (int)((s / nx) % ny), (int)(s / ((long long)nx * ny))};
+        int w3[3] = {v[0], v[1], v[2]};
+        w3[pt.normal_axis] += pt.normal_sign;
+        tab[t] = (int)s;
+        tab[ng + t] = (int)at(w3[0], w3[1], w3[2]);
+        tab[2 * ng + t] = m;
+        tab[3 * ng + t] = pt.kind;
+        // parabolic (or flat) profile over the port's transverse extent, walls halfway
+        double mag = pt.u_max;
+        if (pt.profile == LBCG_PROFILE_PARABOLIC) {
+            for (int a = 0; a < c->D; ++a) {
+                if (a == pt.normal_axis) continue;
+                const double W = (double)(hi[m][a] - lo[m][a] + 1);
+                const double sc = (double)(v[a] - lo[m][a]) + 0.5;
+                mag *= 4.0 * sc * (W - sc) / (W * W);
+            }
+        }
+        double u[3] = {0.0, 0.0, 0.0};
+        u[pt.normal_axis] = mag * pt.normal_sign;
+        gu[t] = u[0];
+        gu[ng + t] = u[1];
+        gu[2 * ng + t] = u[2];
+        gu[3 * ng + t] = pt.rho;
+        gu[4 * ng + t] = pt.psi;
+    }
+    free_tables(c);
+    if (cudaMalloc(&c->d_link, sizeof(uint32_t) * (size_t)n) != cudaSuccess)
+        return fail(LBCG_ERR_NOMEM, "link table allocation failed");
+    if (ng > 0) {
+        if (cudaMalloc(&c->d_ghost, sizeof(int) * tab.size()) != cudaSuccess ||
+            cudaMalloc(&c->d_ghost_u, sizeof(double) * gu.size()) != cudaSuccess) {
+            free_tables(c);
+            return fail(LBCG_ERR_NOMEM, "port table allocation failed");
+        }
+    }
+    if (!c->d_partials) {
+        if (cudaMalloc(&c->d_partials, sizeof(double) * kMaxPartials * kObsSlots) != cudaSuccess ||
+            cudaMalloc(&c->d_result, sizeof(double) * 2 * kObsSlots) != cudaSuccess) {
+            free_tables(c);
+            return fail(LBCG_ERR_NOMEM, "reduction scratch allocation failed");
+        }
+    }
+    LBCG_CUDA(cudaMemcpyAsync(c->d_link, link.data(), sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice,
+                              c->stream),
+              "copy link table");
+    if (ng > 0) {
+        LBCG_CUDA(cudaMemcpyAsync(c->d_ghost, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice,
+                                  c->stream),
+                  "copy ghost table");
+        LBCG_CUDA(cudaMemcpyAsync(c->d_ghost_u, gu.data(), sizeof(double) * gu.size(), cudaMemcpyHostToDevice,
+                                  c->stream),
+                  "copy ghost velocities");
+    }
+    LBCG_CUDA(cudaStreamSynchronize(c->stream), "set_geometry sync");
+    c->mask.assign(mask, mask + n);
+    c->nports = nports;
+    for (int m = 0; m < nports; ++m) c->ports[m] = ports[m];
+    c->nghost = ng;
+    c->any_link = any;
+    c->fluid_sites = fluid;
+    c->geometry = true;
+    c->fields = false;
+    return LBCG_OK;
+}
+
+static int need(lbcg_ctx* c, bool fields)
+{
+    if (!c) return fail(LBCG_ERR_ARG, "null context");
+    if (!c->bound) return fail(LBCG_ERR_STATE, "no state buffers bound");
+    if (!c->geometry) return fail(LBCG_ERR_STATE, "no geometry set");
+    if (fields && !c->fields) return fail(LBCG_ERR_STATE, "no initial fields set");
+    return LBCG_OK;
+}
+
+int lbcg_init_fields_device(lbcg_ctx* c, const double* rr, const double* rb, const double* u)
+{
+    int st = need(c, false);
+    if (st) return st;
+    if (!rr || !rb) return fail(LBCG_ERR_ARG, "null density field");
+    LBCG_CUDA(launch_init(c, rr, rb, u, c->A), "init kernel");
+    c->fields = true;
+    c->step = 0;
+    return LBCG_OK;
+}
+
+int lbcg_init_fields(lbcg_ctx* c, const double* rr, const double* rb, const double* u)
+{
+    int st = need(c, false);
+    if (st) return st;
+    if (!rr || !rb) return fail(LBCG_ERR_ARG, "null density field");
+    // stage in the inactive buffer: rho_r | rho_b | u
+    double* stg = (double*)c->B;
+    const size_t n = (size_t)c->n;
+    LBCG_CUDA(cudaMemcpyAsync(stg, rr, n * 8, cudaMemcpyHostToDevice, c->stream), "copy rho_r");
+    LBCG_CUDA(cudaMemcpyAsync(stg + n, rb, n * 8, cudaMemcpyHostToDevice, c->stream), "copy rho_b");
+    if (u) LBCG_CUDA(cudaMemcpyAsync(stg + 2 * n, u, n * 8 * c->D, cudaMemcpyHostToDevice, c->stream), "copy u");
+    LBCG_CUDA(launch_init(c, stg, stg + n, u ? stg + 2 * n : nullptr, c->A), "init kernel");
+    LBCG_CUDA(cudaStreamSynchronize(c->stream), "init sync");
+    c->fields = true;
+    c->step = 0;
+    return LBCG_OK;
+}
+
+static cudaEvent_t take_event(lbcg_ctx* c, int& idx)
+{
+    idx = -1;
+    for (size_t k = 0; k < c->ev_pool.size(); ++k) {
+        bool used = false;
+        for (auto& pr : c->ev_pending)
+            if (pr.first == (int)k || pr.second == (int)k) used = true;
+        if (!used) {
+            idx = (int)k;
+            return c->ev_pool[k];
+        }
+    }
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->ev_pool.push_back(e);
+    idx = (int)c->ev_pool.size() - 1;
+    return e;
+}
+
+static int drain_events(lbcg_ctx* c)
+{
+    for (auto& pr : c->ev_pending) {
+        LBCG_CUDA(cudaEventSynchronize(c->ev_pool[pr.second]), "event sync");
+        float ms = 0.f;
+        LBCG_CUDA(cudaEventElapsedTime(&ms, c->ev_pool[pr.first], c->ev_pool[pr.second]), "event elapsed");
+        c->timed_ms += ms;
+        c->timed_launches += 1;
+    }
+    c->ev_pending.clear();
+    return LBCG_OK;
+}
+
+int lbcg_step(lbcg_ctx* c, long long nsteps)
+{
+    int st = need(c, true);
+    if (st) return st;
+    if (nsteps < 0) return fail(LBCG_ERR_ARG, "negative step count");
+    for (long long t = 0; t < nsteps; ++t) {
+        if (c->nghost > 0) LBCG_CUDA(launch_fill_ports(c, c->A), "port fill kernel");
+        int i0 = -1, i1 = -1;
+        if (c->timing) {
+            if (c->ev_pending.size() >= 4096) {
+                st = drain_events(c);
+                if (st) return st;
+            }
+            cudaEvent_t e0 = take_event(c, i0);
+            c->ev_pending.push_back({i0, -1});
+            cudaEvent_t e1 = take_event(c, i1);
+            c->ev_pending.back().second = i1;
+            if (!e0 || !e1) return fail(LBCG_ERR_CUDA, "event creation failed");
+            LBCG_CUDA(cudaEventRecord(e0, c->stream), "event record");
+        }
+        LBCG_CUDA(launch_step(c, c->A, c->B), "step kernel");
+        if (c->timing) LBCG_CUDA(cudaEventRecord(c->ev_pool[i1], c->stream), "event record");
+        std::swap(c->A, c->B);
+        c->step += 1;
+    }
+    return LBCG_OK;
+}
+
+long long lbcg_step_count(const lbcg_ctx* c) { return c ? c->step : -1; }
+
+int lbcg_synchronize(lbcg_ctx* c)
+{
+    if (!c) return fail(LBCG_ERR_ARG, "null context");
+    LBCG_CUDA(cudaStreamSynchronize(c->stream), "stream sync");
+    return LBCG_OK;
+}
+
+int lbcg_get_fields_device(lbcg_ctx* c, double* rr, double* rb, double* u)
+{
+    int st = need(c, true);
+    if (st) return st;
+    if (!rr || !rb || !u) return fail(LBCG_ERR_ARG, "null output");
+    LBCG_CUDA(launch_fields(c, c->A, rr, rb, u), "fields kernel");
+    return LBCG_OK;
+}
+
+int lbcg_get_fields(lbcg_ctx* c, double* rr, double* rb, double* u)
+{
+    int st = need(c, true);
+    if (st) return st;
+    if (!rr || !rb || !u) return fail(LBCG_ERR_ARG, "null output");
+    double* stg = (double*)c->B;
+    const size_t n = (size_t)c->n;
+    LBCG_CUDA(launch_fields(c, c->A, stg, stg + n, stg + 2 * n), "fields kernel");
+    LBCG_CUDA(cudaMemcpyAsync(rr, stg, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy rho_r");
+    LBCG_CUDA(cudaMemcpyAsync(rb, stg + n, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy rho_b");
+    LBCG_CUDA(cudaMemcpyAsync(u, stg + 2 * n, n * 8 * c->D, cudaMemcpyDeviceToHost, c->stream), "copy u");
+    LBCG_CUDA(cudaStreamSynchronize(c->stream), "fields sync");
+    return LBCG_OK;
+}
+
+int lbcg_get_populations(lbcg_ctx* c, double* f)
+{
+    int st = need(c, true);
+    if (st) return st;
+    if (!f) return fail(LBCG_ERR_ARG, "null output");
+    double* stg = (double*)c->B;
+    const size_t n = (size_t)c->n;
+    for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < c->Q; ++i) {
+            LBCG_CUDA(launch_pop_plane_to_f64(c, c->A, k, i, stg), "population kernel");
+            LBCG_CUDA(cudaMemcpyAsync(f + ((size_t)k * c->Q + i) * n, stg, n * 8, cudaMemcpyDeviceToHost,
+                                      c->stream),
+                      "copy populations");
+            LBCG_CUDA(cudaStreamSynchronize(c->stream), "populations sync");
+        }
+    return LBCG_OK;
+}
+
+int lbcg_set_populations(lbcg_ctx* c, const double* f)
+{
+    int st = need(c, false);
+    if (st) return st;
+    if (!f) return fail(LBCG_ERR_ARG, "null input");
+    double* stg = (double*)c->B;
+    const size_t n = (size_t)c->n;
+    for (int i = 0; i < c->Q; ++i) {
+        LBCG_CUDA(cudaMemcpyAsync(stg, f + (size_t)i * n, n * 8, cudaMemcpyHostToDevice, c->stream), "copy red");
+        LBCG_CUDA(cudaMemcpyAsync(stg + n, f + ((size_t)c->Q + i) * n, n * 8, cudaMemcpyHostToDevice, c->stream),
+                  "copy blue");
+        LBCG_CUDA(launch_pops_from_f64(c, stg, c->A, i), "population kernel");
+        LBCG_CUDA(cudaStreamSynchronize(c->stream), "populations sync");
+    }
+    c->fields = true;
+    return LBCG_OK;
+}
+
+int lbcg_observables(lbcg_ctx* c, const double centre[3], double r_in, double r_out, lbcg_obs* out)
+{
+    int st = need(c, true);
+    if (st) return st;
+    if (!centre || !out) return fail(LBCG_ERR_ARG, "null centre or output");
+    LBCG_CUDA(launch_observables(c, c->A, centre, r_in, r_out, c->d_partials, c->d_result), "observable kernels");
+    double res[2 * kObsSlots];
+    LBCG_CUDA(cudaMemcpyAsync(res, c->d_result, sizeof(res), cudaMemcpyDeviceToHost, c->stream), "copy result");
+    LBCG_CUDA(cudaStreamSynchronize(c->stream), "observables sync");
+    std::memset(out, 0, sizeof(*out));
+    out->mass_r = res[0];
+    out->mass_b = res[1];
+    out->mom[0] = res[2];
+    out->mom[1] = res[3];
+    out->mom[2] = res[4];
+    out->amount = res[5];
+    out->umax = res[6];
+    out->nonfinite = (int)res[7];
+    out->r_eff = res[8];
+    out->n_in = res[12];
+    out->n_out = res[14];
+    out->p_in = res[12] > 0 ? res[11] / res[12] : 0.0;
+    out->p_out = res[14] > 0 ? res[13] / res[14] : 0.0;
+    out->dp = out->p_in - out->p_out;
+    out->step = c->step;
+    if (out->nonfinite > 0) return fail(LBCG_ERR_DIVERGED, "non-finite or non-positive density at fluid sites");
+    return LBCG_OK;
+}
+
+int lbcg_label(lbcg_ctx* c, int32_t* labels, int64_t* counts, double* volumes, int cap, int* n_drops)
+{
+    int st = need(c, true);
+    if (st) return st;
+    if (!labels || !n_drops || cap < 0) return fail(LBCG_ERR_ARG, "null output");
+    const size_t n = (size_t)c->n;
+    // scratch in the inactive buffer: half[n] doubles | labels[n] ints | flag
+    double* half = (double*)c->B;
+    int32_t* L = (int32_t*)(half + n);
+    int* flag = (int*)(L + n + (n & 1));
+    LBCG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream), "clear flag");
+    LBCG_CUDA(launch_label(c, c->A, L, half, flag), "label kernels");
+    std::vector<double> h(n);
+    int hflag = 0;
+    LBCG_CUDA(cudaMemcpyAsync(labels, L, n * 4, cudaMemcpyDeviceToHost, c->stream), "copy labels");
+    LBCG_CUDA(cudaMemcpyAsync(h.data(), half, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy volumes");
+    LBCG_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy flag");
+    LBCG_CUDA(cudaStreamSynchronize(c->stream), "label sync");
+    if (hflag) return fail(LBCG_ERR_CUDA, "labelling iteration bound reached");
+    // per-droplet count and volume in label order, sums in site order
+    std::vector<int> slot(n, -1);
+    int nd = 0;
+    std::vector<int64_t> cnt;
+    std::vector<double> vol;
+    for (size_t s = 0; s < n; ++s) {
+        const int lab = labels[s];
+        if (lab < 0) continue;
+        if (lab == (int)s) {
+            slot[s] = nd++;
+            cnt.push_back(0);
+            vol.push_back(0.0);
+        }
+        const int k = slot[(size_t)lab];
+        if (k < 0) return fail(LBCG_ERR_CUDA, "label points to a non-root site");
+        cnt[k] += 1;
+        vol[k] += h[s];
+    }
+    for (int k = 0; k < nd && k < cap; ++k) {
+        if (counts) counts[k] = cnt[k];
+        if (volumes) volumes[k] = vol[k];
+    }
+    *n_drops = nd;
+    return LBCG_OK;
+}
+
+int lbcg_set_kernel_timing(lbcg_ctx* c, int enable)
+{
+    if (!c) return fail(LBCG_ERR_ARG, "null context");
+    if (!enable && c->timing) {
+        int st = drain_events(c);
+        if (st) return st;
+    }
+    c->timing = enable != 0;
+    c->timed_ms = 0.0;
+    c->timed_launches = 0;
+    return LBCG_OK;
+}
+
+int lbcg_kernel_time(lbcg_ctx* c, double* total_ms, long long* launches)
+{
+    if (!c || !total_ms || !launches) return fail(LBCG_ERR_ARG, "null argument");
+    int st = drain_events(c);
+    if (st) return st;
+    *total_ms = c->timed_ms;
+    *launches = c->timed_launches;
+    c->timed_ms = 0.0;
+    c->timed_launches = 0;
+    return LBCG_OK;
+}
+
+int lbcg_set_launch(lbcg_ctx* c, int rows, int block_rows)
+{
+    if (!c) return fail(LBCG_ERR_ARG, "null context");
+    if (rows < 0 || block_rows < 0 || (block_rows > 0 && (block_rows < 3 || block_rows > 16)))
+        return fail(LBCG_ERR_ARG, "launch shape out of range (block_rows in 3..16)");
+    c->rows = rows;
+    c->block_rows = block_rows;
+    fill_kparams(c);
+    return LBCG_OK;
+}
+
+}  // extern "C"

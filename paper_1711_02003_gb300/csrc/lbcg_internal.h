@@ -1,0 +1,122 @@
+// lbcg_internal.h -- context structure, kernel parameter block and launcher
+// declarations shared by the translation units of liblbcg.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lbcg.h"
+
+namespace lbcg {
+
+// Per-site link word: bits 0..Q-1 = "pull along direction i bounces back" (the
+// upstream site x - c_i is a wall or outside a closed box face); bits 24..25 = site
+// type (0 fluid, 1 wall, 2 port ghost).
+constexpr uint32_t kTypeShift = 24;
+constexpr uint32_t kTypeFluid = 0, kTypeWall = 1, kTypePort = 2;
+
+// Physical constants in the arithmetic type of a kernel (float or double), so FP32
+// kernels never touch FP64 arithmetic.
+template <typename T>
+struct Phys {
+    T rho0;
+    T half_inv_nu_r, half_inv_nu_b;   // 1/(2 nu_k), nu_k = (tau_k - 1/2)/3
+    T A, beta, psi_wall;
+    T phiR[3], phiB[3];               // phi_i^k per speed class (Eq. 7)
+    T dphiR[3], dphiB[3];             // phi_i^k - w_i per speed class
+    T wr0[3];                         // w_i rho0 per speed class
+    T scale_g, inv_scale_g;           // binary16 total-deviation scale
+};
+
+// Kernel parameter block, passed by value.
+struct KParams {
+    int nx, ny, nz;
+    int per[3];
+    size_t np;              // plane stride (elements)
+    int collision;
+    int lattice;
+    int rows;               // marching length per warp / block
+    int nsx, nsy, nsz;      // strips / blocks per axis
+    Phys<float> pf;
+    Phys<double> pd;
+    double alpha_r, alpha_b;
+};
+
+template <typename T>
+__host__ __device__ inline const Phys<T>& phys(const KParams& P);
+template <>
+__host__ __device__ inline const Phys<float>& phys<float>(const KParams& P) { return P.pf; }
+template <>
+__host__ __device__ inline const Phys<double>& phys<double>(const KParams& P) { return P.pd; }
+
+constexpr int kMaxPartials = 1024;   // blocks of the deterministic reductions
+constexpr int kObsSlots = 16;
+
+}  // namespace lbcg
+
+struct lbcg_ctx {
+    lbcg_params p;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int Q = 9, D = 2;
+    int dims[3] = {1, 1, 1};
+    long long n = 0;        // sites
+    size_t np = 0;          // padded plane length
+    size_t state_bytes = 0;
+    void* A = nullptr;      // current (post-collision) state
+    void* B = nullptr;      // other buffer (scratch between steps)
+    bool bound = false;
+    bool geometry = false;
+    bool fields = false;
+    long long step = 0;
+
+    // geometry tables (library-owned device memory)
+    uint32_t* d_link = nullptr;
+    bool any_link = false;             // any bounce bit or non-fluid site
+    std::vector<uint8_t> mask;
+    int nports = 0;
+    lbcg_port ports[LBCG_MAX_PORTS];
+    int nghost = 0;
+    int* d_ghost = nullptr;            // [4][nghost]: site, inward neighbour, port, kind
+    double* d_ghost_u = nullptr;       // [3][nghost] inlet velocity
+    long long fluid_sites = 0;
+
+    // reductions
+    double* d_partials = nullptr;      // kMaxPartials * kObsSlots
+    double* d_result = nullptr;        // 2 * kObsSlots
+
+    // launch shape
+    int rows = 0, block_rows = 0;
+
+    // kernel timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_pending;
+    double timed_ms = 0.0;
+    long long timed_launches = 0;
+
+    lbcg::KParams kp;
+};
+
+namespace lbcg {
+
+// launchers (step.cu)
+cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b);
+// launchers (aux.cu)
+cudaError_t launch_fill_ports(lbcg_ctx* c, void* a);
+cudaError_t launch_init(lbcg_ctx* c, const double* rr, const double* rb, const double* u, void* a);
+cudaError_t launch_fields(lbcg_ctx* c, const void* a, double* rr, double* rb, double* u);
+cudaError_t launch_pop_plane_to_f64(lbcg_ctx* c, const void* a, int k, int i, double* out);
+cudaError_t launch_pops_from_f64(lbcg_ctx* c, const double* f, void* a, int i);
+cudaError_t launch_observables(lbcg_ctx* c, const void* a, const double centre[3], double r_in, double r_out,
+                               double* d_partials, double* d_result);
+cudaError_t launch_label(lbcg_ctx* c, const void* a, int32_t* parent, double* half, int* d_flag);
+
+void fill_kparams(lbcg_ctx* c);
+size_t storage_size(int precision);
+
+}  // namespace lbcg

@@ -1,0 +1,271 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Gates (element by element on the same seeded inputs):
+  * FP64 storage: populations within 1e-11 absolute after up to 1000 steps;
+  * FP32 deviation storage: rho_R, rho_B, u within 1e-5 relative (max-norm) after
+    1000 steps; Laplace pressure and droplet radius within 1 %;
+  * labels, droplet counts: bit-exact on the same state.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_02003_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_02003_gb300 import build
+    build.build()
+
+
+def _lb():
+    from paper_1711_02003_gb300 import lbcg
+    return lbcg
+
+
+def run_pair(pb, steps, precision=0, **kw):
+    lb = _lb()
+    g = lb.Simulation(pb, precision, **kw)
+    o = oracle.Sim(pb)
+    g.step(steps)
+    o.step(steps)
+    return g, o
+
+
+def relmax(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+# ---------------------------------------------------------------- FP64 populations
+
+def test_fp64_static_droplet_1000_steps():
+    pb = W.static_droplet(W.D2Q9, 64, 16)
+    g, o = run_pair(pb, 1000)
+    assert np.abs(g.populations() - o.populations()).max() <= 1e-11
+
+
+@pytest.mark.parametrize("shape", [(61, 37), (30, 30), (31, 33), (1, 8), (3, 3), (97, 2)])
+def test_fp64_ragged_periodic_two_viscosities(shape):
+    nx, ny = shape
+    pb = W.static_droplet(W.D2Q9, nx, max(1, min(nx, ny) // 4), ny=ny, tau_r=1.7, tau_b=0.8,
+                          centre=(nx // 3, ny // 2, 0))
+    g, o = run_pair(pb, 200)
+    assert np.abs(g.populations() - o.populations()).max() <= 1e-11
+
+
+@pytest.mark.parametrize("outlet", [W.ZERO_GRADIENT_OUTLET, W.PRESSURE_OUTLET])
+def test_fp64_cross_junction_ports_and_walls(outlet):
+    pb = W.cross_junction(nx=130, channel_w=16, side_x=40, side_len=12, u_disp=0.01, u_cont=0.01,
+                          tau_disp=1.5, A=0.01, outlet=outlet, fill_x=30)
+    g, o = run_pair(pb, 400)
+    assert np.abs(g.populations() - o.populations()).max() <= 1e-11
+
+
+def test_fp64_bgk_collision():
+    pb = W.static_droplet(W.D2Q9, 40, 9, tau_r=5.0, tau_b=1.0, collision=W.BGK)
+    g, o = run_pair(pb, 300)
+    assert np.abs(g.populations() - o.populations()).max() <= 1e-11
+
+
+def test_fp64_density_ratio_alpha():
+    pb = W.static_droplet(W.D2Q9, 40, 9).replace(alpha_r=0.6, alpha_b=4 / 9)
+    g, o = run_pair(pb, 200)
+    assert np.abs(g.populations() - o.populations()).max() <= 1e-11
+
+
+@pytest.mark.parametrize("shape", [(24, 20, 18), (31, 17, 5), (33, 3, 4), (5, 5, 1)])
+def test_fp64_d3q19_droplet(shape):
+    nx, ny, nz = shape
+    pb = W.static_droplet(W.D3Q19, nx, max(1, min(shape) // 3), ny=ny, nz=nz, tau_r=1.3, tau_b=0.9,
+                          centre=(nx // 2, ny // 2, nz // 2))
+    g, o = run_pair(pb, 150)
+    assert np.abs(g.populations() - o.populations()).max() <= 1e-11
+
+
+def test_fp64_d3q19_step_emulsifier():
+    pb = W.step_emulsifier(nx=70, ny=20, nz=12, terrace_len=24, terrace_h=4, u_in=0.01, tau_disp=1.4,
+                           fill_x=12)
+    g, o = run_pair(pb, 150)
+    assert np.abs(g.populations() - o.populations()).max() <= 1e-11
+
+
+@pytest.mark.parametrize("rows,block_rows", [(1, 3), (5, 7), (64, 16)])
+def test_launch_shape_does_not_change_results(rows, block_rows):
+    lb = _lb()
+    pb = W.step_emulsifier(nx=50, ny=30, nz=10, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10)
+    a = lb.Simulation(pb, lb.LBCG_FP64)
+    b = lb.Simulation(pb, lb.LBCG_FP64, rows=rows, block_rows=block_rows)
+    a.step(30)
+    b.step(30)
+    assert np.array_equal(a.populations(), b.populations())
+    pb2 = W.static_droplet(W.D2Q9, 70, 12, ny=45)
+    a = lb.Simulation(pb2, lb.LBCG_FP32_DEV)
+    b = lb.Simulation(pb2, lb.LBCG_FP32_DEV, rows=rows)
+    a.step(30)
+    b.step(30)
+    assert np.array_equal(a.populations(), b.populations())
+
+
+def test_deterministic_repeat():
+    lb = _lb()
+    pb = W.cross_junction(nx=130, channel_w=16, side_x=40, side_len=12, fill_x=30)
+    a = lb.Simulation(pb, lb.LBCG_FP32_DEV)
+    b = lb.Simulation(pb, lb.LBCG_FP32_DEV)
+    a.step(100)
+    b.step(100)
+    assert np.array_equal(a.populations(), b.populations())
+
+
+# ---------------------------------------------------------------- FP32 paths
+
+def test_fp32dev_static_droplet_fields_and_laplace():
+    lb = _lb()
+    pb = W.static_droplet(W.D2Q9, 64, 16)
+    g, o = run_pair(pb, 1000, lb.LBCG_FP32_DEV)
+    gr, gb, gu = g.fields()
+    orr, ob, ou = o.fields()
+    assert relmax(gr, orr) <= 1e-5
+    assert relmax(gb, ob) <= 1e-5
+    assert relmax(gu, ou) <= 1e-5
+    go, oo = g.observables((32, 32)), o.observables((32, 32))
+    assert abs(go["dp"] / oo["dp"] - 1) <= 0.01
+    assert abs(go["r_eff"] / oo["r_eff"] - 1) <= 0.01
+
+
+def test_fp32_plain_densities():
+    lb = _lb()
+    pb = W.static_droplet(W.D2Q9, 64, 16)
+    g, o = run_pair(pb, 1000, lb.LBCG_FP32)
+    gr, gb, _ = g.fields()
+    orr, ob, _ = o.fields()
+    assert relmax(gr, orr) <= 1e-5
+    assert relmax(gb, ob) <= 1e-5
+
+
+def test_fp32dev_d3q19_fields():
+    lb = _lb()
+    pb = W.static_droplet(W.D3Q19, 24, 7)
+    g, o = run_pair(pb, 300, lb.LBCG_FP32_DEV)
+    gr, gb, gu = g.fields()
+    orr, ob, ou = o.fields()
+    assert relmax(gr, orr) <= 1e-5 and relmax(gb, ob) <= 1e-5 and relmax(gu, ou) <= 1e-5
+
+
+def test_fp32dev_channel_fields():
+    lb = _lb()
+    pb = W.cross_junction(nx=130, channel_w=16, side_x=40, side_len=12, u_disp=0.005, u_cont=0.005, fill_x=30)
+    g, o = run_pair(pb, 300, lb.LBCG_FP32_DEV)
+    gr, gb, gu = g.fields()
+    orr, ob, ou = o.fields()
+    assert relmax(gr, orr) <= 1e-5 and relmax(gb, ob) <= 1e-5 and relmax(gu, ou) <= 1e-5
+
+
+# ------------------------------------------------------------ observables, labels
+
+def test_observables_match_oracle():
+    lb = _lb()
+    pb = W.static_droplet(W.D2Q9, 64, 16)
+    g, o = run_pair(pb, 300, lb.LBCG_FP64)
+    for rin, rout in ((-1.0, -1.0), (4.0, 25.0)):
+        go, oo = g.observables((32, 32), rin, rout), o.observables((32, 32), rin, rout)
+        assert go["mass_r"] == pytest.approx(oo["mass_r"], rel=1e-13)
+        assert go["mass_b"] == pytest.approx(oo["mass_b"], rel=1e-13)
+        assert np.allclose(go["mom"], oo["mom"], atol=1e-12)
+        assert go["n_in"] == oo["n_in"] and go["n_out"] == oo["n_out"]
+        assert go["p_in"] == pytest.approx(oo["p_in"], rel=1e-13)
+        assert go["p_out"] == pytest.approx(oo["p_out"], rel=1e-13)
+        assert go["dp"] == pytest.approx(oo["dp"], rel=1e-9, abs=1e-14)
+        assert go["r_eff"] == pytest.approx(oo["r_eff"], rel=1e-13)
+        assert go["umax"] == pytest.approx(oo["umax"], rel=1e-9, abs=1e-16)
+
+
+def test_observables_3d_and_mass_conservation():
+    lb = _lb()
+    pb = W.static_droplet(W.D3Q19, 20, 6)
+    g = lb.Simulation(pb, lb.LBCG_FP32_DEV)
+    o0 = g.observables((10, 10, 10))
+    g.step(200)
+    o1 = g.observables((10, 10, 10))
+    assert abs(o1["mass_r"] / o0["mass_r"] - 1) < 1e-6
+    assert abs(o1["mass_b"] / o0["mass_b"] - 1) < 1e-6
+    oo = oracle.Sim(pb)
+    oo.step(200)
+    ref = oo.observables((10, 10, 10))
+    assert abs(o1["dp"] / ref["dp"] - 1) < 0.01
+
+
+def test_labels_bit_exact_same_state():
+    lb = _lb()
+    pb = W.cross_junction(nx=130, channel_w=16, side_x=40, side_len=12, fill_x=30)
+    o = oracle.Sim(pb)
+    o.step(150)
+    f = o.populations()
+    # add three separate red blobs, one across the periodic-free box edge region
+    g = lb.Simulation(pb, lb.LBCG_FP64)
+    g.set_populations(f)
+    gl, gc, gv, gn = g.label()
+    ol, oc, ov, on = o.label()
+    assert gn == on
+    assert np.array_equal(gl, ol)
+    assert np.array_equal(gc, oc)
+    assert np.array_equal(gv, ov)
+
+
+def test_labels_periodic_droplets():
+    lb = _lb()
+    pb = W.static_droplet(W.D3Q19, 16, 4, centre=(0, 8, 15))
+    o = oracle.Sim(pb)
+    g = lb.Simulation(pb, lb.LBCG_FP64)
+    g.set_populations(o.populations())
+    gl, gc, gv, gn = g.label()
+    ol, oc, ov, on = o.label()
+    assert gn == on == 1
+    assert np.array_equal(gl, ol) and np.array_equal(gc, oc) and np.array_equal(gv, ov)
+
+
+def test_population_roundtrip_all_precisions():
+    lb = _lb()
+    pb = W.static_droplet(W.D2Q9, 32, 8)
+    o = oracle.Sim(pb)
+    o.step(20)
+    f = o.populations()
+    for prec, tol in ((lb.LBCG_FP64, 0.0), (lb.LBCG_FP32, 1e-7), (lb.LBCG_FP32_DEV, 1e-7),
+                      (lb.LBCG_FP16_SCALED, 2e-3)):
+        g = lb.Simulation(pb, prec)
+        g.set_populations(f)
+        assert np.abs(g.populations() - f).max() <= tol
+
+
+# ------------------------------------------------------------- full-size workloads
+
+def test_full_size_flow_focuser_fp64_sampled():
+    """1024 x 192 cross junction (the D2Q9 flow-focusing case), FP64, 20 steps: every site."""
+    lb = _lb()
+    pb = W.cross_junction(u_disp=0.005, u_cont=0.005)
+    g, o = run_pair(pb, 20, lb.LBCG_FP64)
+    assert np.abs(g.populations() - o.populations()).max() <= 1e-12
+
+
+def test_full_size_step_emulsifier_fp32dev():
+    """768 x 128 x 32 step emulsifier (the D3Q19 roofline case), FP32 deviation storage,
+    in the launch shape the benchmark times: 2 steps against the oracle at every site,
+    and per-component mass conservation over 20 steps with closed walls."""
+    lb = _lb()
+    pb = W.step_emulsifier()
+    g, o = run_pair(pb, 2, lb.LBCG_FP32_DEV)
+    gr, gb, gu = g.fields()
+    orr, ob, ou = o.fields()
+    assert relmax(gr, orr) <= 1e-6 and relmax(gb, ob) <= 1e-6 and relmax(gu, ou) <= 1e-5
+    closed = pb.replace(ports=[], mask=np.where(pb.mask >= W.PORT0, W.WALL, pb.mask).astype(np.uint8))
+    g = lb.Simulation(closed, lb.LBCG_FP32_DEV)
+    a = g.observables((384, 64, 16))
+    g.step(20)
+    b = g.observables((384, 64, 16))
+    assert abs(b["mass_r"] / a["mass_r"] - 1) < 1e-5 and abs(b["mass_b"] / a["mass_b"] - 1) < 1e-5
