@@ -209,8 +209,11 @@ int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
 
 /* Launch shape of the fused step kernel (0 = library default):
  * rows: sites per warp along the marching axis (D2Q9: y rows per warp strip;
- * D3Q19: z planes per block); block_rows: D3Q19 warps per block along y (>= 3). */
-int lbcg_set_launch(lbcg_ctx* ctx, int rows, int block_rows);
+ * D3Q19: z planes per block); block_rows: D3Q19 warps per block along y (3..16);
+ * variant: 0 default, 1 keep the next row/plane's populations in registers,
+ * 2 re-read them when colliding.  Results are bit-identical across shapes and
+ * variants; only speed changes.  Drops captured step graphs. */
+int lbcg_set_launch(lbcg_ctx* ctx, int rows, int block_rows, int variant);
 
 #ifdef __cplusplus
 }

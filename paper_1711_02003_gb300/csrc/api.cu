@@ -108,6 +108,8 @@ void fill_phys(Phys<T>& ph, const lbcg_params& p, int lattice)
         ph.dphiR[c] = (T)(phR[c] - w[c]);
         ph.dphiB[c] = (T)(phB[c] - w[c]);
         ph.wr0[c] = (T)(w[c] * p.rho0);
+        ph.w[c] = (T)w[c];
+        ph.inv_w[c] = (T)(1.0 / w[c]);
     }
     ph.scale_g = (T)256.0;
     ph.inv_scale_g = (T)(1.0 / 256.0);
@@ -148,7 +150,7 @@ void fill_kparams(lbcg_ctx* c)
         k.nsy = (k.ny + k.rows - 1) / k.rows;
         k.nsz = 1;
     } else {
-        const int wy = c->block_rows > 2 ? c->block_rows : 16;
+        const int wy = c->block_rows > 2 ? c->block_rows : 8;
         c->block_rows = wy;
         k.nsx = (k.nx + 29) / 30;
         k.nsy = (k.ny + (wy - 2) - 1) / (wy - 2);
@@ -165,6 +167,10 @@ void fill_kparams(lbcg_ctx* c)
 }
 
 }  // namespace lbcg
+
+extern "C" {
+static void drop_graphs(lbcg_ctx* c);
+}
 
 static void free_tables(lbcg_ctx* c)
 {
@@ -237,6 +243,8 @@ void lbcg_destroy(lbcg_ctx* c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     free_tables(c);
     cudaFree(c->d_partials);
     cudaFree(c->d_result);
@@ -250,6 +258,7 @@ int lbcg_bind_state(lbcg_ctx* c, void* a, void* b, size_t bytes)
     if (a == b) return fail(LBCG_ERR_ARG, "the two state buffers must differ");
     if (bytes < c->state_bytes) return fail(LBCG_ERR_ARG, "state buffers smaller than lbcg_state_bytes");
     if (((uintptr_t)a | (uintptr_t)b) & 255u) return fail(LBCG_ERR_ARG, "state buffers must be 256-byte aligned");
+    drop_graphs(c);
     c->A = a;
     c->B = b;
     c->bound = true;
@@ -365,6 +374,7 @@ int lbcg_set_geometry(lbcg_ctx* c, const uint8_t* mask, const lbcg_port* ports, 
         gu[3 * ng + t] = pt.rho;
         gu[4 * ng + t] = pt.psi;
     }
+    drop_graphs(c);
     free_tables(c);
     if (cudaMalloc(&c->d_link, sizeof(uint32_t) * (size_t)n) != cudaSuccess)
         return fail(LBCG_ERR_NOMEM, "link table allocation failed");
@@ -443,35 +453,90 @@ int lbcg_init_fields(lbcg_ctx* c, const double* rr, const double* rb, const doub
     return LBCG_OK;
 }
 
-static cudaEvent_t take_event(lbcg_ctx* c, int& idx)
-{
-    idx = -1;
-    for (size_t k = 0; k < c->ev_pool.size(); ++k) {
-        bool used = false;
-        for (auto& pr : c->ev_pending)
-            if (pr.first == (int)k || pr.second == (int)k) used = true;
-        if (!used) {
-            idx = (int)k;
-            return c->ev_pool[k];
-        }
-    }
-    cudaEvent_t e;
-    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-    c->ev_pool.push_back(e);
-    idx = (int)c->ev_pool.size() - 1;
-    return e;
-}
-
 static int drain_events(lbcg_ctx* c)
 {
-    for (auto& pr : c->ev_pending) {
-        LBCG_CUDA(cudaEventSynchronize(c->ev_pool[pr.second]), "event sync");
+    for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+        LBCG_CUDA(cudaEventSynchronize(c->ev_pool[k + 1]), "event sync");
         float ms = 0.f;
-        LBCG_CUDA(cudaEventElapsedTime(&ms, c->ev_pool[pr.first], c->ev_pool[pr.second]), "event elapsed");
+        LBCG_CUDA(cudaEventElapsedTime(&ms, c->ev_pool[k], c->ev_pool[k + 1]), "event elapsed");
         c->timed_ms += ms;
         c->timed_launches += 1;
     }
-    c->ev_pending.clear();
+    c->ev_used = 0;
+    return LBCG_OK;
+}
+
+static int next_events(lbcg_ctx* c, cudaEvent_t& e0, cudaEvent_t& e1)
+{
+    constexpr size_t kMaxPairs = 4096;
+    if (c->ev_used + 2 > 2 * kMaxPairs) {
+        int st = drain_events(c);
+        if (st) return st;
+    }
+    while (c->ev_pool.size() < c->ev_used + 2) {
+        cudaEvent_t e;
+        LBCG_CUDA(cudaEventCreate(&e), "event create");
+        c->ev_pool.push_back(e);
+    }
+    e0 = c->ev_pool[c->ev_used];
+    e1 = c->ev_pool[c->ev_used + 1];
+    c->ev_used += 2;
+    return LBCG_OK;
+}
+
+static void drop_graphs(lbcg_ctx* c)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+        c->graph_start[k] = nullptr;
+    }
+}
+
+// enqueue one step (port refill, fused kernel) on c->stream and swap the buffers
+static int one_step(lbcg_ctx* c)
+{
+    if (c->nghost > 0) LBCG_CUDA(launch_fill_ports(c, c->A), "port fill kernel");
+    LBCG_CUDA(launch_step(c, c->A, c->B), "step kernel");
+    std::swap(c->A, c->B);
+    return LBCG_OK;
+}
+
+// graph of kGraphSteps steps starting from the current buffer A, captured on a private
+// stream (capture is not allowed on the legacy default stream the caller may use)
+static int graph_for_current(lbcg_ctx* c, cudaGraphExec_t& exec)
+{
+    const int k = c->A == c->graph_start[0] ? 0 : (c->A == c->graph_start[1] ? 1 : -1);
+    if (k >= 0 && c->graph[k]) {
+        exec = c->graph[k];
+        return LBCG_OK;
+    }
+    const int slot = c->graph[0] ? 1 : 0;
+    if (!c->cap_stream) LBCG_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "stream create");
+    cudaStream_t user = c->stream;
+    void* a0 = c->A;
+    void* b0 = c->B;
+    c->stream = c->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    int st = LBCG_OK;
+    if (e == cudaSuccess) {
+        for (int t = 0; t < kGraphSteps && st == LBCG_OK; ++t) st = one_step(c);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+        if (st == LBCG_OK && e2 == cudaSuccess) {
+            e = cudaGraphInstantiate(&c->graph[slot], g, 0);
+        } else if (e2 != cudaSuccess) {
+            e = e2;
+        }
+        if (g) cudaGraphDestroy(g);
+    }
+    c->stream = user;
+    c->A = a0;
+    c->B = b0;
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    c->graph_start[slot] = a0;
+    exec = c->graph[slot];
     return LBCG_OK;
 }
 
@@ -480,24 +545,31 @@ int lbcg_step(lbcg_ctx* c, long long nsteps)
     int st = need(c, true);
     if (st) return st;
     if (nsteps < 0) return fail(LBCG_ERR_ARG, "negative step count");
-    for (long long t = 0; t < nsteps; ++t) {
-        if (c->nghost > 0) LBCG_CUDA(launch_fill_ports(c, c->A), "port fill kernel");
-        int i0 = -1, i1 = -1;
-        if (c->timing) {
-            if (c->ev_pending.size() >= 4096) {
-                st = drain_events(c);
-                if (st) return st;
-            }
-            cudaEvent_t e0 = take_event(c, i0);
-            c->ev_pending.push_back({i0, -1});
-            cudaEvent_t e1 = take_event(c, i1);
-            c->ev_pending.back().second = i1;
-            if (!e0 || !e1) return fail(LBCG_ERR_CUDA, "event creation failed");
-            LBCG_CUDA(cudaEventRecord(e0, c->stream), "event record");
+    long long left = nsteps;
+    if (!c->timing && left >= kGraphSteps) {
+        while (left >= kGraphSteps) {
+            cudaGraphExec_t exec = nullptr;
+            st = graph_for_current(c, exec);
+            if (st) return st;
+            LBCG_CUDA(cudaGraphLaunch(exec, c->stream), "graph launch");
+            c->step += kGraphSteps;
+            left -= kGraphSteps;
         }
-        LBCG_CUDA(launch_step(c, c->A, c->B), "step kernel");
-        if (c->timing) LBCG_CUDA(cudaEventRecord(c->ev_pool[i1], c->stream), "event record");
-        std::swap(c->A, c->B);
+    }
+    for (; left > 0; --left) {
+        if (c->timing) {
+            if (c->nghost > 0) LBCG_CUDA(launch_fill_ports(c, c->A), "port fill kernel");
+            cudaEvent_t e0, e1;
+            st = next_events(c, e0, e1);
+            if (st) return st;
+            LBCG_CUDA(cudaEventRecord(e0, c->stream), "event record");
+            LBCG_CUDA(launch_step(c, c->A, c->B), "step kernel");
+            LBCG_CUDA(cudaEventRecord(e1, c->stream), "event record");
+            std::swap(c->A, c->B);
+        } else {
+            st = one_step(c);
+            if (st) return st;
+        }
         c->step += 1;
     }
     return LBCG_OK;
@@ -671,14 +743,17 @@ int lbcg_kernel_time(lbcg_ctx* c, double* total_ms, long long* launches)
     return LBCG_OK;
 }
 
-int lbcg_set_launch(lbcg_ctx* c, int rows, int block_rows)
+int lbcg_set_launch(lbcg_ctx* c, int rows, int block_rows, int variant)
 {
     if (!c) return fail(LBCG_ERR_ARG, "null context");
-    if (rows < 0 || block_rows < 0 || (block_rows > 0 && (block_rows < 3 || block_rows > 16)))
-        return fail(LBCG_ERR_ARG, "launch shape out of range (block_rows in 3..16)");
+    if (rows < 0 || block_rows < 0 || (block_rows > 0 && (block_rows < 3 || block_rows > 8)) || variant < 0 ||
+        variant > 2)
+        return fail(LBCG_ERR_ARG, "launch shape out of range (block_rows in 3..16, variant in 0..2)");
     c->rows = rows;
     c->block_rows = block_rows;
+    c->variant = variant;
     fill_kparams(c);
+    drop_graphs(c);
     return LBCG_OK;
 }
 

@@ -36,7 +36,7 @@ __device__ __forceinline__ void load_rb(const KParams& P, const typename Store<P
         fb = (double)a[(size_t)(Lat<LAT>::Q + i) * P.np + s];
     } else {
         T r, g;
-        SP::load(a, P.np, Lat<LAT>::Q, i, s, phys<T>(P), Lat<LAT>::cls(i), r, g);
+        SP::load(a, (size_t)i * P.np + s, (size_t)(Lat<LAT>::Q + i) * P.np + s, phys<T>(P), Lat<LAT>::cls(i), r, g);
         fr = (double)r;
         fb = ((double)g + P.pd.wr0[Lat<LAT>::cls(i)]) - (double)r;
     }
@@ -55,7 +55,8 @@ __device__ __forceinline__ void store_rb(const KParams& P, typename Store<PREC>:
         a[(size_t)(Lat<LAT>::Q + i) * P.np + s] = (S)fb;
     } else {
         const int c = Lat<LAT>::cls(i);
-        SP::store(a, P.np, Lat<LAT>::Q, i, s, phys<T>(P), c, (T)fr, (T)((fr + fb) - P.pd.wr0[c]));
+        SP::store(a, (size_t)i * P.np + s, (size_t)(Lat<LAT>::Q + i) * P.np + s, phys<T>(P), c, (T)fr,
+                  (T)((fr + fb) - P.pd.wr0[c]));
     }
 }
 

@@ -44,6 +44,9 @@ struct Lat<0> {  // D2Q9
     {
         return cls(i) == 0 ? -4.0 / 27.0 : (cls(i) == 1 ? 2.0 / 27.0 : 5.0 / 108.0);
     }
+    // opposite-direction pairs (p, opp(p)): p = rep(k)
+    static constexpr int NP = 4;
+    __host__ __device__ static constexpr int rep(int k) { return k == 0 ? 1 : (k == 1 ? 2 : (k == 2 ? 5 : 6)); }
 };
 
 template <>
@@ -75,6 +78,8 @@ struct Lat<1> {  // D3Q19
     {
         return cls(i) == 0 ? -1.0 / 3.0 : (cls(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
     }
+    static constexpr int NP = 9;
+    __host__ __device__ static constexpr int rep(int k) { return 2 * k + 1; }
 };
 
 // ---------------------------------------------------------------- storage formats
@@ -89,19 +94,22 @@ template <typename S_, typename T_>
 struct StorePlain {
     using S = S_;
     using T = T_;
-    __device__ static __forceinline__ void load(const S* __restrict__ a, size_t np, int Q, int i, size_t s,
-                                                const Phys<T>& ph, int c, T& r, T& g)
+    // ir: element index of direction i's red plane at the site; ig: of its second plane
+    template <typename IDX>
+    __device__ static __forceinline__ void load(const S* __restrict__ a, IDX ir, IDX ig, const Phys<T>& ph, int c,
+                                                T& r, T& g)
     {
-        const T fr = (T)a[(size_t)i * np + s];
-        const T fb = (T)a[(size_t)(Q + i) * np + s];
+        const T fr = (T)a[ir];
+        const T fb = (T)a[ig];
         r = fr;
         g = (fr + fb) - ph.wr0[c];
     }
-    __device__ static __forceinline__ void store(S* __restrict__ b, size_t np, int Q, int i, size_t s,
-                                                 const Phys<T>& ph, int c, T r, T g)
+    template <typename IDX>
+    __device__ static __forceinline__ void store(S* __restrict__ b, IDX ir, IDX ig, const Phys<T>& ph, int c, T r,
+                                                 T g)
     {
-        b[(size_t)i * np + s] = (S)r;
-        b[(size_t)(Q + i) * np + s] = (S)((g + ph.wr0[c]) - r);
+        b[ir] = (S)r;
+        b[ig] = (S)((g + ph.wr0[c]) - r);
     }
 };
 
@@ -114,17 +122,18 @@ template <>
 struct Store<LBCG_FP32_DEV> {
     using S = float;
     using T = float;
-    __device__ static __forceinline__ void load(const S* __restrict__ a, size_t np, int Q, int i, size_t s,
-                                                const Phys<T>&, int, T& r, T& g)
+    template <typename IDX>
+    __device__ static __forceinline__ void load(const S* __restrict__ a, IDX ir, IDX ig, const Phys<T>&, int, T& r,
+                                                T& g)
     {
-        r = a[(size_t)i * np + s];
-        g = a[(size_t)(Q + i) * np + s];
+        r = a[ir];
+        g = a[ig];
     }
-    __device__ static __forceinline__ void store(S* __restrict__ b, size_t np, int Q, int i, size_t s,
-                                                 const Phys<T>&, int, T r, T g)
+    template <typename IDX>
+    __device__ static __forceinline__ void store(S* __restrict__ b, IDX ir, IDX ig, const Phys<T>&, int, T r, T g)
     {
-        b[(size_t)i * np + s] = r;
-        b[(size_t)(Q + i) * np + s] = g;
+        b[ir] = r;
+        b[ig] = g;
     }
 };
 
@@ -134,28 +143,22 @@ template <>
 struct Store<LBCG_FP16_SCALED> {
     using S = __half;
     using T = float;
-    __device__ static __forceinline__ float wcls(int Q, int c)
+    __device__ static __forceinline__ float wcls(int c, const Phys<T>& ph) { return ph.wr0[c] / ph.rho0; }
+    template <typename IDX>
+    __device__ static __forceinline__ void load(const S* __restrict__ a, IDX ir, IDX ig, const Phys<T>& ph, int c,
+                                                T& r, T& g)
     {
-        return Q == 9 ? (c == 0 ? 4.0f / 9.0f : (c == 1 ? 1.0f / 9.0f : 1.0f / 36.0f))
-                      : (c == 0 ? 1.0f / 3.0f : (c == 1 ? 1.0f / 18.0f : 1.0f / 36.0f));
+        const float wi = ph.w[c];
+        r = __half2float(a[ir]) * wi + 0.5f * ph.wr0[c];
+        g = __half2float(a[ig]) * (wi * ph.inv_scale_g);
     }
-    __device__ static __forceinline__ float iwcls(int Q, int c)
+    template <typename IDX>
+    __device__ static __forceinline__ void store(S* __restrict__ b, IDX ir, IDX ig, const Phys<T>& ph, int c, T r,
+                                                 T g)
     {
-        return Q == 9 ? (c == 0 ? 2.25f : (c == 1 ? 9.0f : 36.0f)) : (c == 0 ? 3.0f : (c == 1 ? 18.0f : 36.0f));
-    }
-    __device__ static __forceinline__ void load(const S* __restrict__ a, size_t np, int Q, int i, size_t s,
-                                                const Phys<T>& ph, int c, T& r, T& g)
-    {
-        const float wi = wcls(Q, c);
-        r = __half2float(a[(size_t)i * np + s]) * wi + 0.5f * ph.wr0[c];
-        g = __half2float(a[(size_t)(Q + i) * np + s]) * (wi * ph.inv_scale_g);
-    }
-    __device__ static __forceinline__ void store(S* __restrict__ b, size_t np, int Q, int i, size_t s,
-                                                 const Phys<T>& ph, int c, T r, T g)
-    {
-        const float iw = iwcls(Q, c);
-        b[(size_t)i * np + s] = __float2half_rn((r - 0.5f * ph.wr0[c]) * iw);
-        b[(size_t)(Q + i) * np + s] = __float2half_rn(g * (iw * ph.scale_g));
+        const float iw = ph.inv_w[c];
+        b[ir] = __float2half_rn((r - 0.5f * ph.wr0[c]) * iw);
+        b[ig] = __float2half_rn(g * (iw * ph.scale_g));
     }
 };
 
@@ -165,22 +168,35 @@ struct Store<LBCG_FP16_SCALED> {
 // Steps (Eq. 4 read as a sequence): moments (Eqs. 2-3), mixture relaxation time,
 // equilibrium (Eqs. 6-7), regularized relaxation (Eq. 11) or BGK (Eq. 5),
 // perturbation (Eq. 9), recolouring (Eq. 10).
+//
+// Evaluation by opposite-direction pairs (p, q = opp(p), c_q = -c_p): the
+// equilibrium, the Hermite term of Eq. 11 and the perturbation are sums of a part
+// even in c (shared by p and q) and a part odd in c (equal and opposite), so each
+// pair is computed once: g_p = S + A, g_q = S - A; the recolouring split likewise
+// r_p = X + Y, r_q = X - Y.  The second moment Pi of the non-equilibrium only sees
+// the even parts.  The same quantities as a direction-by-direction evaluation, in
+// fewer operations.
 template <int LAT, typename T>
 __device__ __forceinline__ void collide_site(const KParams& P, const Phys<T>& ph, T (&r)[Lat<LAT>::Q],
                                              T (&g)[Lat<LAT>::Q], const T F[3])
 {
     using L = Lat<LAT>;
-    constexpr int Q = L::Q;
+    constexpr int NP = L::NP;
     const T rho0 = ph.rho0;
 
-    T rhoR = 0, sg = 0, jx = 0, jy = 0, jz = 0;
+    // moments (Eqs. 2-3)
+    T rhoR = r[0], sg = g[0], jx = 0, jy = 0, jz = 0;
+    T ge[NP], go[NP];  // even and odd halves of each pair
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        rhoR += r[i];
-        sg += g[i];
-        if (L::cx(i)) jx += L::cx(i) > 0 ? g[i] : -g[i];
-        if (L::cy(i)) jy += L::cy(i) > 0 ? g[i] : -g[i];
-        if (L::D == 3 && L::cz(i)) jz += L::cz(i) > 0 ? g[i] : -g[i];
+    for (int k = 0; k < NP; ++k) {
+        const int p = L::rep(k), q = L::opp(p);
+        rhoR += r[p] + r[q];
+        ge[k] = g[p] + g[q];
+        go[k] = g[p] - g[q];
+        sg += ge[k];
+        if (L::cx(p)) jx += L::cx(p) > 0 ? go[k] : -go[k];
+        if (L::cy(p)) jy += L::cy(p) > 0 ? go[k] : -go[k];
+        if (L::D == 3 && L::cz(p)) jz += L::cz(p) > 0 ? go[k] : -go[k];
     }
     const T rho = rho0 + sg;
     const T rhoB = rho - rhoR;
@@ -193,27 +209,39 @@ __device__ __forceinline__ void collide_site(const KParams& P, const Phys<T>& ph
     const T tau = T(3) / inv_nu + T(0.5);
     const T om1 = T(1) - T(1) / tau;
 
+    // equilibrium (Eqs. 6-7) as deviation from w_i rho0: even part eS, odd part eA
     const T usq = ux * ux + uy * uy + uz * uz;
-    const T drho = sg;  // rho - rho0
-    T geq[Q];
+    const T base = sg - T(1.5) * rho * usq;              // drho - 1.5 rho u^2
+    const T dphi0 = rhoR * ph.dphiR[0] + rhoB * ph.dphiB[0];
+    const T dphi1 = rhoR * ph.dphiR[1] + rhoB * ph.dphiB[1];
+    const T dphi2 = rhoR * ph.dphiR[2] + rhoB * ph.dphiB[2];
+    const T eq0 = (T)L::w(0) * base + dphi0;
+    T eS[NP], eA[NP];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const T cu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
-        const T wi = (T)L::w(i);
-        const int c = L::cls(i);
-        const T dphi = rhoR * ph.dphiR[c] + rhoB * ph.dphiB[c];
-        geq[i] = wi * drho + dphi + rho * wi * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq);
+    for (int k = 0; k < NP; ++k) {
+        const int p = L::rep(k);
+        const T cu = (T)L::cx(p) * ux + (T)L::cy(p) * uy + (T)L::cz(p) * uz;
+        const T wi = (T)L::w(p);
+        eS[k] = wi * (base + T(4.5) * rho * cu * cu) + (L::cls(p) == 1 ? dphi1 : dphi2);
+        eA[k] = (T(3) * wi) * rho * cu;
     }
 
+    T gS[NP], gA[NP], g0;
     if (P.collision == LBCG_BGK) {
+        g0 = eq0 + om1 * (g[0] - eq0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = geq[i] + om1 * (g[i] - geq[i]);
+        for (int k = 0; k < NP; ++k) {
+            gS[k] = eS[k] + om1 * (T(0.5) * ge[k] - eS[k]);
+            gA[k] = eA[k] + om1 * (T(0.5) * go[k] - eA[k]);
+        }
     } else {
+        // Pi^neq = sum_i (g_i - geq_i) c_i c_i: only even parts contribute
         T pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const T ne = g[i] - geq[i];
-            const int ax = L::cx(i), ay = L::cy(i), az = L::cz(i);
+        for (int k = 0; k < NP; ++k) {
+            const int p = L::rep(k);
+            const T ne = ge[k] - T(2) * eS[k];
+            const int ax = L::cx(p), ay = L::cy(p), az = L::cz(p);
             if (ax) pxx += ne;
             if (ay) pyy += ne;
             if (az) pzz += ne;
@@ -221,42 +249,64 @@ __device__ __forceinline__ void collide_site(const KParams& P, const Phys<T>& ph
             if (ax && az) pxz += (ax * az > 0) ? ne : -ne;
             if (ay && az) pyz += (ay * az > 0) ? ne : -ne;
         }
-        const T third = T(1) / T(3);
+        const T tr3 = (pxx + pyy + pzz) * (T(1) / T(3));
+        g0 = eq0 + om1 * (T(4.5) * (T)L::w(0)) * (-tr3);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int ax = L::cx(i), ay = L::cy(i), az = L::cz(i);
-            T qp = ((T)(ax * ax) - third) * pxx + ((T)(ay * ay) - third) * pyy;
-            if (L::D == 3) qp += ((T)(az * az) - third) * pzz;
+        for (int k = 0; k < NP; ++k) {
+            const int p = L::rep(k);
+            const int ax = L::cx(p), ay = L::cy(p), az = L::cz(p);
+            T qp = -tr3;
+            if (ax) qp += pxx;
+            if (ay) qp += pyy;
+            if (az) qp += pzz;
             if (ax && ay) qp += T(2 * ax * ay) * pxy;
             if (ax && az) qp += T(2 * ax * az) * pxz;
             if (ay && az) qp += T(2 * ay * az) * pyz;
-            g[i] = geq[i] + om1 * (T(4.5) * (T)L::w(i)) * qp;
+            gS[k] = eS[k] + om1 * (T(4.5) * (T)L::w(p)) * qp;
+            gA[k] = eA[k];
         }
     }
 
-    // perturbation (Eq. 9) and recolouring (Eq. 10)
+    // perturbation (Eq. 9): even in c
     const T fn2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
     const bool has_f = fn2 > T(1e-20);
     const T fn = has_f ? sqrt(fn2) : T(0);
     const T inv_fn = has_f ? T(1) / fn : T(0);
     const T inv_fn2 = inv_fn * inv_fn;
     const T half_a_fn = T(0.5) * ph.A * fn;
+    T fcs[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int p = L::rep(k);
+        fcs[k] = (T)L::cx(p) * F[0] + (T)L::cy(p) * F[1] + (T)L::cz(p) * F[2];
+        if (has_f) gS[k] += half_a_fn * ((T)L::w(p) * fcs[k] * fcs[k] * inv_fn2 - (T)L::Bc(p));
+    }
+    if (has_f) g0 -= half_a_fn * (T)L::Bc(0);
+
+    // recolouring (Eq. 10).  It keeps rho_R of the site exactly; the rest direction
+    // (cos phi_0 = 0) takes rho_R minus the other directions, so the FP32 rounding of
+    // the sum cannot repeat step after step at a static interface and drift.
     const T seg = ph.beta * rhoR * rhoB * inv_rho * inv_rho;
     const T fracR = rhoR * inv_rho;
     const T inv_sqrt2 = T(0.70710678118654752440);
+    const T e1 = rhoR * ph.phiR[1] + rhoB * ph.phiB[1];
+    const T e2 = rhoR * ph.phiR[2] + rhoB * ph.phiB[2];
+    T rsum = 0;
+    g[0] = g0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const T fc = (T)L::cx(i) * F[0] + (T)L::cy(i) * F[1] + (T)L::cz(i) * F[2];
-        const T wi = (T)L::w(i);
-        T gpost = g[i];
-        if (has_f) gpost += half_a_fn * (wi * fc * fc * inv_fn2 - (T)L::Bc(i));
-        const int c = L::cls(i);
-        const T cosphi = (c == 0) ? T(0) : (c == 1 ? fc * inv_fn : fc * inv_fn * inv_sqrt2);
-        const T e = rhoR * ph.phiR[c] + rhoB * ph.phiB[c];
-        const T ftot = gpost + ph.wr0[c];
-        r[i] = fracR * ftot + seg * cosphi * e;
-        g[i] = gpost;
+    for (int k = 0; k < NP; ++k) {
+        const int p = L::rep(k), q = L::opp(p);
+        const int c = L::cls(p);
+        const T cosphi = c == 1 ? fcs[k] * inv_fn : fcs[k] * inv_fn * inv_sqrt2;
+        const T X = fracR * (gS[k] + ph.wr0[c]);
+        const T Y = fracR * gA[k] + seg * cosphi * (c == 1 ? e1 : e2);
+        g[p] = gS[k] + gA[k];
+        g[q] = gS[k] - gA[k];
+        r[p] = X + Y;
+        r[q] = X - Y;
+        rsum += r[p] + r[q];
     }
+    r[0] = rhoR - rsum;
 }
 
 }  // namespace lbcg

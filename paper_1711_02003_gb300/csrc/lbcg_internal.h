@@ -29,6 +29,7 @@ struct Phys {
     T phiR[3], phiB[3];               // phi_i^k per speed class (Eq. 7)
     T dphiR[3], dphiB[3];             // phi_i^k - w_i per speed class
     T wr0[3];                         // w_i rho0 per speed class
+    T w[3], inv_w[3];                 // w_i and 1/w_i per speed class
     T scale_g, inv_scale_g;           // binary16 total-deviation scale
 };
 
@@ -55,6 +56,7 @@ __host__ __device__ inline const Phys<double>& phys<double>(const KParams& P) { 
 
 constexpr int kMaxPartials = 1024;   // blocks of the deterministic reductions
 constexpr int kObsSlots = 16;
+constexpr int kGraphSteps = 32;   // steps per captured graph (even: A/B roles return)
 
 }  // namespace lbcg
 
@@ -90,14 +92,19 @@ struct lbcg_ctx {
     double* d_result = nullptr;        // 2 * kObsSlots
 
     // launch shape
-    int rows = 0, block_rows = 0;
+    int rows = 0, block_rows = 0, variant = 0;
 
-    // kernel timing
+    // kernel timing: event pairs 2k, 2k+1 bracket the k-th timed launch since the last drain
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, int>> ev_pending;
+    size_t ev_used = 0;
     double timed_ms = 0.0;
     long long timed_launches = 0;
+
+    // CUDA graphs of kGraphSteps steps, one per starting buffer, captured on a private stream
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    void* graph_start[2] = {nullptr, nullptr};
 
     lbcg::KParams kp;
 };

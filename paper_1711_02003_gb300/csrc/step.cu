@@ -16,8 +16,12 @@
 //          the ring) and marches along y.  psi of rows y-1, y, y+1 sits in
 //          registers; x-neighbours come from warp shuffles.  No shared memory, no
 //          block barrier.
-//   D3Q19: one block owns 30 x (rows-2) sites in x-y (ring lanes and ring warps)
+//   D3Q19: one block owns 30 x (WY-2) sites in x-y (ring lanes and ring warps)
 //          and marches along z; psi of four z-planes is staged in shared memory.
+//
+// Element offsets are 32-bit when all 2Q planes fit below 2^31 elements (IDX = int),
+// 64-bit otherwise.  Upstream offsets are site-index differences precomputed per
+// lane (x), row (y) and plane (z), so periodic wrap costs nothing per direction.
 #include "lbcg_device.cuh"
 
 namespace lbcg {
@@ -38,57 +42,91 @@ __device__ __forceinline__ bool wrap_coord(int v, int n, int per, int& vs)
     return false;
 }
 
-// upstream neighbours (x - 1, x + 1) clamped into the box; a clamped one is only
-// reached through a bounce-back link, so its value is never used
-__device__ __forceinline__ void nbrs(int vs, int n, int per, int& vm, int& vp)
+// offsets (in sites along this axis) to the upstream neighbours vs-1 and vs+1; a
+// neighbour outside a closed axis is clamped to vs (reached only through a
+// bounce-back link, so never read)
+__device__ __forceinline__ void nbr_off(int vs, int n, int per, int& dm, int& dp)
 {
-    vm = vs - 1 >= 0 ? vs - 1 : (per ? n - 1 : 0);
-    vp = vs + 1 < n ? vs + 1 : (per ? 0 : n - 1);
+    dm = vs - 1 >= 0 ? -1 : (per ? n - 1 : 0);
+    dp = vs + 1 < n ? 1 : (per ? -(n - 1) : 0);
 }
 
-// Streamed populations (pull, Eq. 1) of the fluid site (xs, ys, zs) into r/g and
-// its psi.  Upstream of direction i is x - c_i.
-template <int LAT, int PREC>
-__device__ __forceinline__ typename Store<PREC>::T pull_fluid(
-    const KParams& P, const typename Store<PREC>::S* __restrict__ A, int xs, int xm, int xp, int ys, int ym,
-    int yp, int zs, int zm, int zp, uint32_t lk, typename Store<PREC>::T (&r)[Lat<LAT>::Q],
-    typename Store<PREC>::T (&g)[Lat<LAT>::Q])
+// site-index offsets of the upstream neighbours: *m for c_axis = +1 (pull from the
+// minus side), *p for c_axis = -1
+struct Up {
+    int xm, xp;
+    long long ym, yp;
+    long long zm, zp;
+};
+
+template <int LAT, typename IDX>
+__device__ __forceinline__ IDX up_off(const Up& u, int i)
+{
+    using L = Lat<LAT>;
+    IDX d = 0;
+    if (L::cx(i) > 0) d += (IDX)u.xm;
+    if (L::cx(i) < 0) d += (IDX)u.xp;
+    if (L::cy(i) > 0) d += (IDX)u.ym;
+    if (L::cy(i) < 0) d += (IDX)u.yp;
+    if (L::cz(i) > 0) d += (IDX)u.zm;
+    if (L::cz(i) < 0) d += (IDX)u.zp;
+    return d;
+}
+
+// Streamed populations (pull, Eq. 1) of the fluid site s into r/g; returns its psi.
+template <int LAT, int PREC, typename IDX>
+__device__ __forceinline__ typename Store<PREC>::T pull_fluid(const KParams& P,
+                                                              const typename Store<PREC>::S* __restrict__ A, IDX s,
+                                                              const Up& u, uint32_t lk,
+                                                              typename Store<PREC>::T (&r)[Lat<LAT>::Q],
+                                                              typename Store<PREC>::T (&g)[Lat<LAT>::Q])
 {
     using L = Lat<LAT>;
     using SP = Store<PREC>;
     using T = typename SP::T;
     constexpr int Q = L::Q;
-    const size_t self = (size_t)xs + (size_t)P.nx * ((size_t)ys + (size_t)P.ny * (size_t)zs);
-    T rr = 0, sg = 0;
+    const IDX np = (IDX)P.np;
+    const Phys<T>& ph = phys<T>(P);
+    constexpr uint32_t qmask = (1u << Q) - 1u;
+    if ((lk & qmask) == 0u) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int sx = L::cx(i) > 0 ? xm : (L::cx(i) < 0 ? xp : xs);
-        const int sy = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : ys);
-        const int sz = L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : zs);
-        const size_t src = (size_t)sx + (size_t)P.nx * ((size_t)sy + (size_t)P.ny * (size_t)sz);
-        const bool bounce = (lk >> i) & 1u;
-        SP::load(A, P.np, Q, bounce ? L::opp(i) : i, bounce ? self : src, phys<T>(P), L::cls(i), r[i], g[i]);
+        for (int i = 0; i < Q; ++i) {
+            const IDX ir = (IDX)i * np + s + up_off<LAT, IDX>(u, i);
+            SP::load(A, ir, ir + (IDX)Q * np, ph, L::cls(i), r[i], g[i]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const bool bounce = (lk >> i) & 1u;
+            const IDX ir = bounce ? (IDX)L::opp(i) * np + s : (IDX)i * np + s + up_off<LAT, IDX>(u, i);
+            SP::load(A, ir, ir + (IDX)Q * np, ph, L::cls(i), r[i], g[i]);
+        }
+    }
+    T rr = r[0], sg = g[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
         rr += r[i];
         sg += g[i];
     }
-    const T rho = phys<T>(P).rho0 + sg;
+    const T rho = ph.rho0 + sg;
     return (rr - (rho - rr)) / rho;
 }
 
 // psi of a port ghost site from its own (already filled) populations
-template <int LAT, int PREC>
+template <int LAT, int PREC, typename IDX>
 __device__ __forceinline__ typename Store<PREC>::T ghost_psi(const KParams& P,
-                                                             const typename Store<PREC>::S* __restrict__ A,
-                                                             size_t s)
+                                                             const typename Store<PREC>::S* __restrict__ A, IDX s)
 {
     using L = Lat<LAT>;
     using SP = Store<PREC>;
     using T = typename SP::T;
+    const IDX np = (IDX)P.np;
     T rr = 0, sg = 0;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         T r, g;
-        SP::load(A, P.np, L::Q, i, s, phys<T>(P), L::cls(i), r, g);
+        const IDX ir = (IDX)i * np + s;
+        SP::load(A, ir, ir + (IDX)L::Q * np, phys<T>(P), L::cls(i), r, g);
         rr += r;
         sg += g;
     }
@@ -96,19 +134,23 @@ __device__ __forceinline__ typename Store<PREC>::T ghost_psi(const KParams& P,
     return (rr - (rho - rr)) / rho;
 }
 
-template <int LAT, int PREC>
-__device__ __forceinline__ void store_site(const KParams& P, typename Store<PREC>::S* __restrict__ B, size_t s,
+template <int LAT, int PREC, typename IDX>
+__device__ __forceinline__ void store_site(const KParams& P, typename Store<PREC>::S* __restrict__ B, IDX s,
                                            const typename Store<PREC>::T (&r)[Lat<LAT>::Q],
                                            const typename Store<PREC>::T (&g)[Lat<LAT>::Q])
 {
     using L = Lat<LAT>;
     using T = typename Store<PREC>::T;
+    const IDX np = (IDX)P.np;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) Store<PREC>::store(B, P.np, L::Q, i, s, phys<T>(P), L::cls(i), r[i], g[i]);
+    for (int i = 0; i < L::Q; ++i) {
+        const IDX ir = (IDX)i * np + s;
+        Store<PREC>::store(B, ir, ir + (IDX)L::Q * np, phys<T>(P), L::cls(i), r[i], g[i]);
+    }
 }
 
 // ------------------------------------------------------------------------ D2Q9
-template <int PREC>
+template <int PREC, typename IDX>
 __global__ void __launch_bounds__(256) k_step_d2q9(const KParams P, const typename Store<PREC>::S* __restrict__ A,
                                                    typename Store<PREC>::S* __restrict__ B,
                                                    const uint32_t* __restrict__ link)
@@ -125,8 +167,9 @@ __global__ void __launch_bounds__(256) k_step_d2q9(const KParams P, const typena
     int xs;
     const bool xok = wrap_coord(x, nx, P.per[0], xs) && x <= nx;
     const bool xint = lane >= 1 && lane <= 30 && x < nx;
-    int xm, xp;
-    nbrs(xs, nx, P.per[0], xm, xp);
+    Up u;
+    nbr_off(xs, nx, P.per[0], u.xm, u.xp);
+    u.zm = u.zp = 0;
     const int y0 = syi * P.rows;
     const int y1 = min(y0 + P.rows, ny);
     const T psi_wall = phys<T>(P).psi_wall;
@@ -134,57 +177,63 @@ __global__ void __launch_bounds__(256) k_step_d2q9(const KParams P, const typena
     T psi_a = psi_wall, psi_b = psi_wall;  // rows yy-2, yy-1
     T rb[Q], gb[Q];                        // populations of row yy-1
     bool coll_b = false;
+    IDX s_b = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) rb[i] = gb[i] = T(0);
 
     for (int yy = y0 - 1; yy <= y1; ++yy) {
         int ys;
         const bool yok = wrap_coord(yy, ny, P.per[1], ys);
-        int ym, yp;
-        nbrs(ys, ny, P.per[1], ym, yp);
+        int dym, dyp;
+        nbr_off(ys, ny, P.per[1], dym, dyp);
+        u.ym = (long long)dym * nx;
+        u.yp = (long long)dyp * nx;
         T rn[Q], gn[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) rn[i] = gn[i] = T(0);
         T psi_n = psi_wall;
         bool fluid_n = false;
+        const IDX s = (IDX)xs + (IDX)nx * (IDX)ys;
         if (xok && yok) {
-            const size_t s = (size_t)xs + (size_t)nx * (size_t)ys;
             const uint32_t lk = link ? __ldg(link + s) : 0u;
             const uint32_t type = (lk >> kTypeShift) & 3u;
             if (type == kTypeFluid) {
-                psi_n = pull_fluid<0, PREC>(P, A, xs, xm, xp, ys, ym, yp, 0, 0, 0, lk, rn, gn);
+                psi_n = pull_fluid<0, PREC, IDX>(P, A, s, u, lk, rn, gn);
                 fluid_n = true;
             } else if (type == kTypePort) {
-                psi_n = ghost_psi<0, PREC>(P, A, s);
+                psi_n = ghost_psi<0, PREC, IDX>(P, A, s);
             }
         }
         if (yy - 1 >= y0) {  // warp-uniform: collide row yy-1
             const T am = __shfl_up_sync(0xffffffffu, psi_a, 1), ap = __shfl_down_sync(0xffffffffu, psi_a, 1);
             const T bm = __shfl_up_sync(0xffffffffu, psi_b, 1), bp = __shfl_down_sync(0xffffffffu, psi_b, 1);
-            const T nm = __shfl_up_sync(0xffffffffu, psi_n, 1), np = __shfl_down_sync(0xffffffffu, psi_n, 1);
+            const T nm = __shfl_up_sync(0xffffffffu, psi_n, 1), np_ = __shfl_down_sync(0xffffffffu, psi_n, 1);
             if (coll_b) {
-                // neighbour psi in direction order; the row index is cy: -1 -> a, 0 -> b, +1 -> n
+                // F = 3 sum_p w_p (psi(x + c_p) - psi(x - c_p)) c_p; rows by cy: -1 a, 0 b, +1 n
+                auto nb = [&](int cx, int cy) -> T {
+                    return cy < 0 ? (cx < 0 ? am : (cx > 0 ? ap : psi_a))
+                         : cy > 0 ? (cx < 0 ? nm : (cx > 0 ? np_ : psi_n))
+                                  : (cx < 0 ? bm : (cx > 0 ? bp : psi_b));
+                };
                 T F[3] = {T(0), T(0), T(0)};
 #pragma unroll
-                for (int i = 1; i < Q; ++i) {
-                    const int cx = L::cx(i), cy = L::cy(i);
-                    const T v = cy < 0 ? (cx < 0 ? am : (cx > 0 ? ap : psi_a))
-                              : cy > 0 ? (cx < 0 ? nm : (cx > 0 ? np : psi_n))
-                                       : (cx < 0 ? bm : (cx > 0 ? bp : psi_b));
-                    const T wv = (T)L::w(i) * v;
-                    if (cx) F[0] += cx > 0 ? wv : -wv;
-                    if (cy) F[1] += cy > 0 ? wv : -wv;
+                for (int k = 0; k < L::NP; ++k) {
+                    const int p = L::rep(k);
+                    const int cx = L::cx(p), cy = L::cy(p);
+                    const T d = (T)L::w(p) * (nb(cx, cy) - nb(-cx, -cy));
+                    if (cx) F[0] += cx > 0 ? d : -d;
+                    if (cy) F[1] += cy > 0 ? d : -d;
                 }
                 F[0] *= T(3);
                 F[1] *= T(3);
                 collide_site<0, T>(P, phys<T>(P), rb, gb, F);
-                int yc = yy - 1;
-                store_site<0, PREC>(P, B, (size_t)xs + (size_t)nx * (size_t)yc, rb, gb);
+                store_site<0, PREC, IDX>(P, B, s_b, rb, gb);
             }
         }
         psi_a = psi_b;
         psi_b = psi_n;
         coll_b = fluid_n && xint && yy >= y0 && yy < y1;
+        s_b = s;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             rb[i] = rn[i];
@@ -195,10 +244,11 @@ __global__ void __launch_bounds__(256) k_step_d2q9(const KParams P, const typena
 
 // ----------------------------------------------------------------------- D3Q19
 // blockDim = (32, WY); warp w owns row y = by*(WY-2) + w - 1; rows 1..WY-2 collide.
-template <int PREC, bool KEEP>
-__global__ void __launch_bounds__(512) k_step_d3q19(const KParams P, const typename Store<PREC>::S* __restrict__ A,
-                                                    typename Store<PREC>::S* __restrict__ B,
-                                                    const uint32_t* __restrict__ link)
+template <int PREC, bool KEEP, typename IDX>
+__global__ void __launch_bounds__(256, 2) k_step_d3q19(const KParams P,
+                                                       const typename Store<PREC>::S* __restrict__ A,
+                                                       typename Store<PREC>::S* __restrict__ B,
+                                                       const uint32_t* __restrict__ link)
 {
     using T = typename Store<PREC>::T;
     using L = Lat<1>;
@@ -209,15 +259,22 @@ __global__ void __launch_bounds__(512) k_step_d3q19(const KParams P, const typen
     const int w = threadIdx.y;
     const int WY = blockDim.y;
     const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const long long nxy = (long long)nx * ny;
     const int x = blockIdx.x * 30 + lane - 1;
     const int y = blockIdx.y * (WY - 2) + w - 1;
     int xs, ys;
     const bool xok = wrap_coord(x, nx, P.per[0], xs) && x <= nx;
     const bool yok = wrap_coord(y, ny, P.per[1], ys) && y <= ny;
     const bool inner = lane >= 1 && lane <= 30 && x < nx && w >= 1 && w <= WY - 2 && y < ny;
-    int xm, xp, ym, yp;
-    nbrs(xs, nx, P.per[0], xm, xp);
-    nbrs(ys, ny, P.per[1], ym, yp);
+    Up u;
+    {
+        int a, b;
+        nbr_off(xs, nx, P.per[0], u.xm, u.xp);
+        nbr_off(ys, ny, P.per[1], a, b);
+        u.ym = (long long)a * nx;
+        u.yp = (long long)b * nx;
+    }
+    const IDX sxy = (IDX)xs + (IDX)nx * (IDX)ys;
     const int z0 = blockIdx.z * P.rows;
     const int z1 = min(z0 + P.rows, nz);
     const T psi_wall = phys<T>(P).psi_wall;
@@ -230,22 +287,26 @@ __global__ void __launch_bounds__(512) k_step_d3q19(const KParams P, const typen
     for (int zz = z0 - 1; zz <= z1; ++zz) {
         int zs;
         const bool zok = wrap_coord(zz, nz, P.per[2], zs);
-        int zm, zp;
-        nbrs(zs, nz, P.per[2], zm, zp);
+        {
+            int a, b;
+            nbr_off(zs, nz, P.per[2], a, b);
+            u.zm = (long long)a * nxy;
+            u.zp = (long long)b * nxy;
+        }
         T rn[Q], gn[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) rn[i] = gn[i] = T(0);
         T psi_n = psi_wall;
         bool fluid_n = false;
+        const IDX s = sxy + (IDX)nxy * (IDX)zs;
         if (xok && yok && zok) {
-            const size_t s = (size_t)xs + (size_t)nx * ((size_t)ys + (size_t)ny * (size_t)zs);
             const uint32_t lk = link ? __ldg(link + s) : 0u;
             const uint32_t type = (lk >> kTypeShift) & 3u;
             if (type == kTypeFluid) {
-                psi_n = pull_fluid<1, PREC>(P, A, xs, xm, xp, ys, ym, yp, zs, zm, zp, lk, rn, gn);
+                psi_n = pull_fluid<1, PREC, IDX>(P, A, s, u, lk, rn, gn);
                 fluid_n = true;
             } else if (type == kTypePort) {
-                psi_n = ghost_psi<1, PREC>(P, A, s);
+                psi_n = ghost_psi<1, PREC, IDX>(P, A, s);
             }
         }
         const int slot_n = (zz - z0 + 1) & 3;
@@ -253,29 +314,35 @@ __global__ void __launch_bounds__(512) k_step_d3q19(const KParams P, const typen
         __syncthreads();
         if (zz - 1 >= z0 && coll_b) {
             const int zc = zz - 1;
-            int zcs = zc, zcm, zcp;
-            nbrs(zcs, nz, P.per[2], zcm, zcp);
+            const IDX sc = sxy + (IDX)nxy * (IDX)zc;
             if (!KEEP) {
-                const size_t s = (size_t)xs + (size_t)nx * ((size_t)ys + (size_t)ny * (size_t)zcs);
-                const uint32_t lk = link ? __ldg(link + s) : 0u;
-                pull_fluid<1, PREC>(P, A, xs, xm, xp, ys, ym, yp, zcs, zcm, zcp, lk, rb, gb);
+                int a, b;
+                nbr_off(zc, nz, P.per[2], a, b);
+                Up uc = u;
+                uc.zm = (long long)a * nxy;
+                uc.zp = (long long)b * nxy;
+                const uint32_t lk = link ? __ldg(link + sc) : 0u;
+                pull_fluid<1, PREC, IDX>(P, A, sc, uc, lk, rb, gb);
             }
+            auto nb = [&](int cx, int cy, int cz) -> T {
+                const int slot = (zc + cz - z0 + 1) & 3;
+                return psi_s[(slot * WY + (w + cy)) * 32 + (lane + cx)];
+            };
             T F[3] = {T(0), T(0), T(0)};
 #pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-                const int slot = (zc + cz - z0 + 1) & 3;
-                const T v = psi_s[(slot * WY + (w + cy)) * 32 + (lane + cx)];
-                const T wv = (T)L::w(i) * v;
-                if (cx) F[0] += cx > 0 ? wv : -wv;
-                if (cy) F[1] += cy > 0 ? wv : -wv;
-                if (cz) F[2] += cz > 0 ? wv : -wv;
+            for (int k = 0; k < L::NP; ++k) {
+                const int p = L::rep(k);
+                const int cx = L::cx(p), cy = L::cy(p), cz = L::cz(p);
+                const T d = (T)L::w(p) * (nb(cx, cy, cz) - nb(-cx, -cy, -cz));
+                if (cx) F[0] += cx > 0 ? d : -d;
+                if (cy) F[1] += cy > 0 ? d : -d;
+                if (cz) F[2] += cz > 0 ? d : -d;
             }
             F[0] *= T(3);
             F[1] *= T(3);
             F[2] *= T(3);
             collide_site<1, T>(P, phys<T>(P), rb, gb, F);
-            store_site<1, PREC>(P, B, (size_t)xs + (size_t)nx * ((size_t)ys + (size_t)ny * (size_t)zcs), rb, gb);
+            store_site<1, PREC, IDX>(P, B, sc, rb, gb);
         }
         coll_b = fluid_n && inner && zz >= z0 && zz < z1;
         if (KEEP) {
@@ -289,6 +356,8 @@ __global__ void __launch_bounds__(512) k_step_d3q19(const KParams P, const typen
 }
 
 // ---------------------------------------------------------------------- launchers
+static bool small_index(const lbcg_ctx* c) { return (long long)2 * c->Q * (long long)c->np < (1LL << 31) - 1; }
+
 template <int PREC>
 static cudaError_t launch_d2q9(lbcg_ctx* c, const void* a, void* b)
 {
@@ -297,8 +366,11 @@ static cudaError_t launch_d2q9(lbcg_ctx* c, const void* a, void* b)
     const long long warps = (long long)P.nsx * P.nsy;
     const int threads = 256;
     const long long blocks = (warps * 32 + threads - 1) / threads;
-    k_step_d2q9<PREC><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b,
-                                                                    c->any_link ? c->d_link : nullptr);
+    const uint32_t* lk = c->any_link ? c->d_link : nullptr;
+    if (small_index(c))
+        k_step_d2q9<PREC, int><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk);
+    else
+        k_step_d2q9<PREC, long long><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk);
     return cudaGetLastError();
 }
 
@@ -312,8 +384,11 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b)
     dim3 block(32, wy);
     dim3 grid(P.nsx, P.nsy, P.nsz);
     size_t smem = 4 * (size_t)wy * 32 * sizeof(T);
-    k_step_d3q19<PREC, KEEP><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b,
-                                                                c->any_link ? c->d_link : nullptr);
+    const uint32_t* lk = c->any_link ? c->d_link : nullptr;
+    if (small_index(c))
+        k_step_d3q19<PREC, KEEP, int><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk);
+    else
+        k_step_d3q19<PREC, KEEP, long long><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk);
     return cudaGetLastError();
 }
 
@@ -328,11 +403,19 @@ cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b)
             case LBCG_FP16_SCALED: return launch_d2q9<LBCG_FP16_SCALED>(c, a, b);
         }
     } else {
+        // default: FP64 re-reads the collided plane (register budget), others keep it
+        const bool keep = c->variant == 1 || (c->variant == 0 && prec != LBCG_FP64);
         switch (prec) {
-            case LBCG_FP64: return launch_d3q19<LBCG_FP64, false>(c, a, b);
-            case LBCG_FP32: return launch_d3q19<LBCG_FP32, true>(c, a, b);
-            case LBCG_FP32_DEV: return launch_d3q19<LBCG_FP32_DEV, true>(c, a, b);
-            case LBCG_FP16_SCALED: return launch_d3q19<LBCG_FP16_SCALED, true>(c, a, b);
+            case LBCG_FP64:
+                return keep ? launch_d3q19<LBCG_FP64, true>(c, a, b) : launch_d3q19<LBCG_FP64, false>(c, a, b);
+            case LBCG_FP32:
+                return keep ? launch_d3q19<LBCG_FP32, true>(c, a, b) : launch_d3q19<LBCG_FP32, false>(c, a, b);
+            case LBCG_FP32_DEV:
+                return keep ? launch_d3q19<LBCG_FP32_DEV, true>(c, a, b)
+                            : launch_d3q19<LBCG_FP32_DEV, false>(c, a, b);
+            case LBCG_FP16_SCALED:
+                return keep ? launch_d3q19<LBCG_FP16_SCALED, true>(c, a, b)
+                            : launch_d3q19<LBCG_FP16_SCALED, false>(c, a, b);
         }
     }
     return cudaErrorInvalidValue;

@@ -79,7 +79,7 @@ _PROTOS = {
     "lbcg_label": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.POINTER(C.c_int)]),
     "lbcg_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
     "lbcg_kernel_time": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong)]),
-    "lbcg_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "lbcg_set_launch": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
 }
 
 
@@ -144,7 +144,7 @@ class Simulation:
     Calls are enqueued on ``stream`` (a torch.cuda.Stream; default: the current stream)."""
 
     def __init__(self, pb, precision: int = LBCG_FP32_DEV, stream=None, init: bool = True, rows: int = 0,
-                 block_rows: int = 0):
+                 block_rows: int = 0, variant: int = 0):
         import torch
         L = load()
         self.pb = pb
@@ -163,8 +163,8 @@ class Simulation:
             self._b = torch.empty(self.state_bytes, dtype=torch.uint8, device="cuda")
         _check("lbcg_bind_state", L.lbcg_bind_state(h, _vp(self._a.data_ptr()), _vp(self._b.data_ptr()),
                                                     self.state_bytes))
-        if rows or block_rows:
-            self.set_launch(rows, block_rows)
+        if rows or block_rows or variant:
+            self.set_launch(rows, block_rows, variant)
         mask = np.ascontiguousarray(np.asarray(pb.mask, np.uint8).ravel())
         ports = ports_of(pb)
         _check("lbcg_set_geometry", L.lbcg_set_geometry(h, _ptr(mask), ports, len(pb.ports)))
@@ -183,8 +183,8 @@ class Simulation:
             pass
 
     # ---------------------------------------------------------------- calls
-    def set_launch(self, rows: int = 0, block_rows: int = 0):
-        _check("lbcg_set_launch", _lib.lbcg_set_launch(self._h, int(rows), int(block_rows)))
+    def set_launch(self, rows: int = 0, block_rows: int = 0, variant: int = 0):
+        _check("lbcg_set_launch", _lib.lbcg_set_launch(self._h, int(rows), int(block_rows), int(variant)))
 
     def init_fields(self, rho_r, rho_b, u=None):
         rr = np.ascontiguousarray(rho_r, np.float64).ravel()

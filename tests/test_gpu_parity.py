@@ -80,11 +80,30 @@ def test_fp64_density_ratio_alpha():
     assert np.abs(g.populations() - o.populations()).max() <= 1e-11
 
 
-@pytest.mark.parametrize("shape", [(24, 20, 18), (31, 17, 5), (33, 3, 4), (5, 5, 1)])
+def slab(pb):
+    """Red slab x in [nx/4, 3nx/4): planar interfaces (for boxes too small for a droplet)."""
+    x = np.arange(pb.nsites) % pb.nx
+    psi = np.where((x >= pb.nx // 4) & (x < (3 * pb.nx) // 4), 1.0, -1.0)
+    return pb.replace(rho_r=(1 + psi) / 2, rho_b=(1 - psi) / 2)
+
+
+# A D3Q19 droplet centred ON a lattice site is an unstable equilibrium of the discrete
+# recolouring dynamics (it drifts off the site once rounding breaks the symmetry, and
+# 1e-16 differences grow to 1e-2), so field-level parity cases centre droplets between
+# sites, where perturbations stay at their initial size.
+@pytest.mark.parametrize("shape", [(24, 20, 18), (31, 17, 5)])
 def test_fp64_d3q19_droplet(shape):
     nx, ny, nz = shape
-    pb = W.static_droplet(W.D3Q19, nx, max(1, min(shape) // 3), ny=ny, nz=nz, tau_r=1.3, tau_b=0.9,
-                          centre=(nx // 2, ny // 2, nz // 2))
+    pb = W.static_droplet(W.D3Q19, nx, min(shape) // 3 + 0.5, ny=ny, nz=nz, tau_r=1.3, tau_b=0.9,
+                          centre=(nx / 2 - 0.5, ny / 2 - 0.5, nz / 2 - 0.5))
+    g, o = run_pair(pb, 150)
+    assert np.abs(g.populations() - o.populations()).max() <= 1e-11
+
+
+@pytest.mark.parametrize("shape", [(33, 3, 4), (5, 5, 1), (1, 7, 3)])
+def test_fp64_d3q19_tiny_boxes(shape):
+    nx, ny, nz = shape
+    pb = slab(W.static_droplet(W.D3Q19, nx, 1, ny=ny, nz=nz, tau_r=1.3, tau_b=0.9))
     g, o = run_pair(pb, 150)
     assert np.abs(g.populations() - o.populations()).max() <= 1e-11
 
@@ -96,7 +115,7 @@ def test_fp64_d3q19_step_emulsifier():
     assert np.abs(g.populations() - o.populations()).max() <= 1e-11
 
 
-@pytest.mark.parametrize("rows,block_rows", [(1, 3), (5, 7), (64, 16)])
+@pytest.mark.parametrize("rows,block_rows", [(1, 3), (5, 7), (64, 8)])
 def test_launch_shape_does_not_change_results(rows, block_rows):
     lb = _lb()
     pb = W.step_emulsifier(nx=50, ny=30, nz=10, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10)
@@ -151,8 +170,8 @@ def test_fp32_plain_densities():
 
 def test_fp32dev_d3q19_fields():
     lb = _lb()
-    pb = W.static_droplet(W.D3Q19, 24, 7)
-    g, o = run_pair(pb, 300, lb.LBCG_FP32_DEV)
+    pb = W.static_droplet(W.D3Q19, 24, 7, centre=(11.5, 11.5, 11.5))
+    g, o = run_pair(pb, 1000, lb.LBCG_FP32_DEV)
     gr, gb, gu = g.fields()
     orr, ob, ou = o.fields()
     assert relmax(gr, orr) <= 1e-5 and relmax(gb, ob) <= 1e-5 and relmax(gu, ou) <= 1e-5
@@ -188,16 +207,17 @@ def test_observables_match_oracle():
 
 def test_observables_3d_and_mass_conservation():
     lb = _lb()
-    pb = W.static_droplet(W.D3Q19, 20, 6)
+    c = (9.5, 9.5, 9.5)
+    pb = W.static_droplet(W.D3Q19, 20, 6, centre=c)
     g = lb.Simulation(pb, lb.LBCG_FP32_DEV)
-    o0 = g.observables((10, 10, 10))
+    o0 = g.observables(c)
     g.step(200)
-    o1 = g.observables((10, 10, 10))
+    o1 = g.observables(c)
     assert abs(o1["mass_r"] / o0["mass_r"] - 1) < 1e-6
     assert abs(o1["mass_b"] / o0["mass_b"] - 1) < 1e-6
     oo = oracle.Sim(pb)
     oo.step(200)
-    ref = oo.observables((10, 10, 10))
+    ref = oo.observables(c)
     assert abs(o1["dp"] / ref["dp"] - 1) < 0.01
 
 
