@@ -139,28 +139,25 @@ void fill_kparams(lbcg_ctx* c)
     fill_phys(k.pd, c->p, c->p.lattice);
     const int sms = 152;
     if (c->p.lattice == LBCG_D2Q9) {
+        // strips of 30 x rows sites per warp; rows trade the ring re-reads (2/rows) against
+        // enough warps for about four waves of 24 resident warps per SM (measured best: 16-32)
         k.nsx = (k.nx + 29) / 30;
         int rows = c->rows;
         if (rows <= 0) {
-            const long long target = (long long)sms * 24 * 3;  // about three waves of warps
+            const long long target = (long long)sms * 24 * 4;
             long long r = ((long long)k.nsx * k.ny) / target;
-            rows = (int)std::max(4LL, std::min(64LL, r));
+            rows = (int)std::max(4LL, std::min(32LL, r));
         }
         k.rows = std::min(rows, k.ny);
         k.nsy = (k.ny + k.rows - 1) / k.rows;
         k.nsz = 1;
     } else {
+        // blocks of 32 x 8 threads (two resident per SM) marching 8 z-planes (measured best)
         const int wy = c->block_rows > 2 ? c->block_rows : 8;
         c->block_rows = wy;
         k.nsx = (k.nx + 29) / 30;
         k.nsy = (k.ny + (wy - 2) - 1) / (wy - 2);
-        int rows = c->rows;
-        if (rows <= 0) {
-            const long long per_slab = (long long)k.nsx * k.nsy;
-            const long long want = (long long)sms * 3;
-            long long nsz = (want + per_slab - 1) / per_slab;
-            rows = (int)std::max(4LL, std::min(64LL, (k.nz + nsz - 1) / std::max(1LL, nsz)));
-        }
+        const int rows = c->rows > 0 ? c->rows : 8;
         k.rows = std::min(rows, k.nz);
         k.nsz = (k.nz + k.rows - 1) / k.rows;
     }

@@ -144,6 +144,10 @@ def test_deterministic_repeat():
 
 # ---------------------------------------------------------------- FP32 paths
 
+# Velocity in a resting droplet is the spurious current alone (about 5e-5 after 1000
+# steps in 2D, 1e-6 for the off-site 3D droplet); FP32 rounding of the force-like terms
+# leaves about 2e-9 absolute velocity error, so u is gated at 1e-5 relative only where
+# the flow has a velocity scale (channels below) and against the spurious-current size here.
 def test_fp32dev_static_droplet_fields_and_laplace():
     lb = _lb()
     pb = W.static_droplet(W.D2Q9, 64, 16)
@@ -152,10 +156,12 @@ def test_fp32dev_static_droplet_fields_and_laplace():
     orr, ob, ou = o.fields()
     assert relmax(gr, orr) <= 1e-5
     assert relmax(gb, ob) <= 1e-5
-    assert relmax(gu, ou) <= 1e-5
+    assert np.abs(gu - ou).max() <= 1e-8
+    assert relmax(gu, ou) <= 2e-4
     go, oo = g.observables((32, 32)), o.observables((32, 32))
     assert abs(go["dp"] / oo["dp"] - 1) <= 0.01
     assert abs(go["r_eff"] / oo["r_eff"] - 1) <= 0.01
+    assert abs(go["umax"] / oo["umax"] - 1) <= 0.01
 
 
 def test_fp32_plain_densities():
@@ -170,17 +176,22 @@ def test_fp32_plain_densities():
 
 def test_fp32dev_d3q19_fields():
     lb = _lb()
-    pb = W.static_droplet(W.D3Q19, 24, 7, centre=(11.5, 11.5, 11.5))
+    c = (11.5, 11.5, 11.5)
+    pb = W.static_droplet(W.D3Q19, 24, 7, centre=c)
     g, o = run_pair(pb, 1000, lb.LBCG_FP32_DEV)
     gr, gb, gu = g.fields()
     orr, ob, ou = o.fields()
-    assert relmax(gr, orr) <= 1e-5 and relmax(gb, ob) <= 1e-5 and relmax(gu, ou) <= 1e-5
+    assert relmax(gr, orr) <= 1e-5 and relmax(gb, ob) <= 1e-5
+    assert np.abs(gu - ou).max() <= 1e-8
+    go, oo = g.observables(c), o.observables(c)
+    assert abs(go["dp"] / oo["dp"] - 1) <= 0.01
+    assert abs(go["r_eff"] / oo["r_eff"] - 1) <= 0.01
 
 
 def test_fp32dev_channel_fields():
     lb = _lb()
     pb = W.cross_junction(nx=130, channel_w=16, side_x=40, side_len=12, u_disp=0.005, u_cont=0.005, fill_x=30)
-    g, o = run_pair(pb, 300, lb.LBCG_FP32_DEV)
+    g, o = run_pair(pb, 1000, lb.LBCG_FP32_DEV)
     gr, gb, gu = g.fields()
     orr, ob, ou = o.fields()
     assert relmax(gr, orr) <= 1e-5 and relmax(gb, ob) <= 1e-5 and relmax(gu, ou) <= 1e-5
