@@ -193,6 +193,37 @@ int lbcg_set_populations(lbcg_ctx* ctx, const double* host_f);
  * filled) when nonfinite > 0. */
 int lbcg_observables(lbcg_ctx* ctx, const double centre[3], double r_in, double r_out, lbcg_obs* out);
 
+/* Allocation-free observables.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory, e.g. code recording a CUDA graph by
+ * stream capture (cudaMalloc cannot be captured), plug-ins whose host application
+ * owns every device allocation through its own pool, or loops that forbid allocation
+ * after start-up.  It needs no context and allocates nothing: the caller passes the
+ * inputs and receives the result; the reduction's scratch is a file-scope device
+ * array of 131,328 bytes (1024 partial rows of 16 doubles plus 2 result rows) that
+ * every GPU loading the library holds until the process exits.
+ *   p        lattice, box and storage precision of the state (validated as by
+ *            lbcg_create; LBCG_ERR_ARG otherwise)
+ *   dev_state device buffer holding one population state in the layout of
+ *            lbcg_state_bytes(p) (e.g. the buffer of a context that holds its current
+ *            state); read only
+ *   dev_mask device array of nsites mask codes (only code 0 = fluid is counted), or
+ *            NULL when every site is fluid
+ *   centre, r_in, r_out   as for lbcg_observables
+ *   stream   CUDA stream of the kernels (NULL = legacy default); the call waits for it
+ *   out      host result; out->step = -1 (no context)
+ * Results equal those of lbcg_observables for the same state.  The reduction launches
+ * at most 1024 blocks whatever the lattice size, so every lattice the library accepts
+ * fits; a request needing more partial rows than the array holds is rejected with
+ * LBCG_ERR_CAPACITY.  The first call on each device looks up the array's device
+ * address with cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the last
+ * call's contents (every row a call reads is written by that call first): calls whose
+ * GPU work overlaps, on different streams or host threads, race and must be ordered
+ * by the caller.  Returns LBCG_ERR_DIVERGED (out filled) when a fluid site has a
+ * non-finite or non-positive density. */
+int lbcg_observables_noalloc(const lbcg_params* p, const void* dev_state, const uint8_t* dev_mask,
+                             const double centre[3], double r_in, double r_out, void* stream, lbcg_obs* out);
+
 /* Droplet labelling: connected components of {fluid sites with rho_R > rho_B}
  * (psi > 0), face-connected, wrapping periodic axes.  labels[nsites] receives the
  * smallest linear site index of the site's component, or -1.  counts/volumes (may be

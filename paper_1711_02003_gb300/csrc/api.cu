@@ -670,6 +670,18 @@ int lbcg_observables(lbcg_ctx* c, const double centre[3], double r_in, double r_
     return LBCG_OK;
 }
 
+int lbcg_observables_noalloc(const lbcg_params* p, const void* dev_state, const uint8_t* dev_mask,
+                             const double centre[3], double r_in, double r_out, void* stream, lbcg_obs* out)
+{
+    int st = validate(p);
+    if (st) return st;
+    if (!dev_state || !centre || !out) return fail(LBCG_ERR_ARG, "null state, centre or output");
+    std::string err;
+    st = noalloc_observables(p, dev_state, dev_mask, centre, r_in, r_out, stream, out, err);
+    if (st) return fail(st, err);
+    return LBCG_OK;
+}
+
 int lbcg_label(lbcg_ctx* c, int32_t* labels, int64_t* counts, double* volumes, int cap, int* n_drops)
 {
     int st = need(c, true);

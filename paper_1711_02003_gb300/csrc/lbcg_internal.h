@@ -124,6 +124,9 @@ cudaError_t launch_observables(lbcg_ctx* c, const void* a, const double centre[3
 cudaError_t launch_label(lbcg_ctx* c, const void* a, int32_t* parent, double* half, int* d_flag);
 
 void fill_kparams(lbcg_ctx* c);
+// noalloc.cu
+int noalloc_observables(const lbcg_params* p, const void* state, const uint8_t* mask, const double centre[3],
+                        double r_in, double r_out, void* stream, lbcg_obs* out, std::string& err);
 size_t storage_size(int precision);
 
 }  // namespace lbcg

@@ -77,6 +77,8 @@ _PROTOS = {
     "lbcg_set_populations": (C.c_int, [_vp, _vp]),
     "lbcg_observables": (C.c_int, [_vp, _dp, C.c_double, C.c_double, C.POINTER(lbcg_obs)]),
     "lbcg_label": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.POINTER(C.c_int)]),
+    "lbcg_observables_noalloc": (C.c_int, [C.POINTER(lbcg_params), _vp, _vp, _dp, C.c_double, C.c_double, _vp,
+                                           C.POINTER(lbcg_obs)]),
     "lbcg_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
     "lbcg_kernel_time": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong)]),
     "lbcg_set_launch": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
