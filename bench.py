@@ -113,14 +113,22 @@ def dist_setup():
     return world, rank, local
 
 
-def reduce_max(v: float, world: int) -> float:
+def reduce_max(v: float, world: int, device: str = "cuda") -> float:
+    """Max over ranks (the slowest replica sets the job's time)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_mlups(units_per_rank: float, world: int, ms_local: float, device: str = "cuda") -> tuple:
+    """Whole-job throughput of `world` replicas: all ranks' site updates over the max-over-ranks
+    time.  Returns (MLUPS, max ms)."""
+    ms_max = reduce_max(ms_local, world, device)
+    return world * units_per_rank / (ms_max * 1e-3) / 1e6, ms_max
 
 
 def barrier(world: int):
@@ -130,7 +138,8 @@ def barrier(world: int):
 
 
 def cpu_oracle_sample(pb, budget_s: float = 12.0):
-    """Time the FP64 oracle on the same workload: whole-box steps until budget_s."""
+    """Time the FP64 oracle on the same workload: whole-box steps until budget_s.
+    Returns the cpu_baseline record and the oracle (advanced by the timed steps)."""
     import oracle
     s = oracle.Sim(pb)
     fluid = pb.fluid_sites()
@@ -142,31 +151,69 @@ def cpu_oracle_sample(pb, budget_s: float = 12.0):
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": fluid * n / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{n} full-box step(s) of the same workload ({fluid} fluid sites), FP64, OpenMP over "
-                      f"{oracle.threads()} host threads, {dt:.1f} s"}
+    rec = {"value": fluid * n / dt / 1e6, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
+           "sample": f"{n} full-box step(s) of the same workload ({fluid} fluid sites), FP64, OpenMP over "
+                     f"{oracle.threads()} host threads, {dt:.1f} s"}
+    return rec, s
 
 
-def run_reference(args, world, rank):
-    """The oracle timed as the reference arm (host cores)."""
+def error_vs_oracle(sim, osim) -> dict:
+    """Max-norm relative error of the GPU fields against the FP64 oracle after the same steps."""
+    gr, gb, gu = sim.fields()
+    orr, ob, ou = osim.fields()
+
+    def rel(a, b):
+        return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+    return {"steps": int(osim.step_count), "rho_r": rel(gr, orr), "rho_b": rel(gb, ob), "u": rel(gu, ou),
+            "u_abs": float(np.abs(gu - ou).max())}
+
+
+def serving_sample(n_requests: int, steps_scale: float, baseline_n: int, rate: float = 20.0) -> dict:
+    """Continuous-batching serving of the mixed request workload (FP32-dev batches under a
+    150 GB HBM budget) and the one-at-a-time FP64 baseline on the first requests."""
+    from paper_1711_02003_gb300 import serve
+    reqs = serve.make_requests(n_requests, rate=rate, seed=0, steps_scale=steps_scale)
+    eng = serve.LbcgEngine(precision=PREC["f32dev"], max_slots=64)
+    srv = serve.Server(eng, hbm_budget=150e9, chunk=100)
+    res = srv.run(reqs, realtime=True)
+    out = {"requests": n_requests, "arrival_rate_per_s": rate, "steps_scale": steps_scale, "hbm_budget_gb": 150,
+           "precision": "f32dev", "peak_resident": srv.peak_resident, "peak_hbm_gb": srv.peak_used / 1e9}
+    out.update({k: v for k, v in serve.summary(res).items()})
+    if baseline_n:
+        base = serve.run_one_at_a_time(reqs[:baseline_n], precision=PREC["f64"])
+        bs = serve.summary(base)
+        out["baseline_one_at_a_time_f64"] = {"requests": baseline_n, "p50_s": bs["p50_s"], "p99_s": bs["p99_s"],
+                                             "aggregate_mlups": bs["aggregate_mlups"]}
+    return out
+
+
+def run_reference(args, world, rank, budget_s: float = 120.0):
+    """The oracle timed as the reference arm on the host cores: full-box steps of the same
+    workload, at most K timed steps and at most budget_s seconds (a bounded sample)."""
     if rank != 0:
         return
     pb, desc, _ = make_workload(args.workload)
     import oracle
     s = oracle.Sim(pb)
     fluid = pb.fluid_sites()
-    for _ in range(args.warmup):
-        s.step(1)
+    warm = min(args.warmup, 3)
+    s.step(warm)
+    n = 0
     t0 = time.perf_counter()
-    s.step(args.steps)
+    while n < args.steps:
+        s.step(1)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
     dt = time.perf_counter() - t0
-    v = fluid * args.steps / dt / 1e6
+    v = fluid * n / dt / 1e6
     line = {"impl": "reference", "metric": "two-fluid MLUPS", "value": v, "unit": "MLUPS", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "precision": "f64 oracle (CPU)", "fluid_sites": fluid},
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
-                             "sample": f"{args.steps} timed full-box steps after {args.warmup} warm-up"},
+                             "sample": f"{n} timed full-box steps (of {args.steps} requested, {budget_s:.0f} s cap) "
+                                       f"after {warm} warm-up, FP64, OpenMP over {oracle.threads()} host threads"},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -174,13 +221,16 @@ def run_reference(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="lbcg", choices=["lbcg", "reference"])
     ap.add_argument("--workload", default="step_emulsifier")
     ap.add_argument("--precision", default="f32dev", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--serving-requests", type=int, default=64, help="0 disables the serving sample")
+    ap.add_argument("--serving-steps-scale", type=float, default=0.25)
+    ap.add_argument("--serving-baseline", type=int, default=6)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -226,8 +276,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     kms, klaunch = sim.kernel_time()
     sim.set_kernel_timing(False)
-    ms_max = reduce_max(ms, world)
-    value = world * fluid * args.steps / (ms_max * 1e-3) / 1e6
+    value, ms_max = aggregate_mlups(fluid * args.steps, world, ms)
     obs = sim.observables(centre, allow_diverged=True)
     port_launch = 1 if pb.ports else 0
     launches = args.steps * (1 + port_launch) + n_obs * 4
@@ -271,8 +320,15 @@ def main():
     if rank != 0:
         return
     cpu = None
+    err = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(pb, args.cpu_budget)
+        cpu, osim = cpu_oracle_sample(pb, args.cpu_budget)
+        sim.init_fields(pb.rho_r, pb.rho_b, pb.u)
+        sim.step(osim.step_count)
+        err = error_vs_oracle(sim, osim)
+    serving = None
+    if world == 1 and args.serving_requests > 0:
+        serving = serving_sample(args.serving_requests, args.serving_steps_scale, args.serving_baseline)
     clocks = clk.summary()
     line = {
         "metric": "two-fluid MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -292,6 +348,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "error_vs_f64_oracle": err,
+        "serving": serving,
         "observables": {"mass_r": obs["mass_r"], "mass_b": obs["mass_b"], "umax": obs["umax"],
                         "nonfinite": obs["nonfinite"]},
     }

@@ -23,11 +23,13 @@
  *     the legacy default stream).  Calls taking HOST pointers copy synchronously
  *     and return after the copy; calls taking DEVICE pointers are asynchronous
  *     on that stream.
- *   - The library allocates only small device tables (per-site link flags,
- *     port ghost lists, reduction partials) at lbcg_set_geometry.  The two
- *     population buffers are owned by the caller (e.g. torch tensors) and bound
- *     with lbcg_bind_state; between steps the inactive buffer is used as scratch
- *     by read-back, labelling and initialisation calls.
+ *   - The two population buffers are owned by the caller (e.g. torch tensors)
+ *     and bound with lbcg_bind_state.  The library allocates device tables
+ *     (per-site link flags, port ghost lists, reduction partials) at
+ *     lbcg_set_geometry, and a staging / read-back scratch on the first call that
+ *     needs one (kept until lbcg_destroy).  Both state buffers hold a defined value
+ *     at every site: initialisation writes both, steps write fluid sites and refill
+ *     port ghosts, wall sites stay zero.
  *   - Per-site arrays are indexed site = x + nx*(y + ny*z), x fastest.
  *   - Population layout seen through lbcg_get_populations/lbcg_set_populations:
  *     FP64 [k][i][site], k = 0 red, 1 blue, directions 0-based with 0 = rest:
@@ -232,6 +234,35 @@ int lbcg_observables_noalloc(const lbcg_params* p, const void* dev_state, const 
  * Synchronous. */
 int lbcg_label(lbcg_ctx* ctx, int32_t* labels, int64_t* counts, double* volumes, int cap, int* n_drops);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent instances (contexts of one lattice and storage precision) advanced
+ * together: each chunk of up to 32 steps replays one captured CUDA graph whose nodes run
+ * the port refill and the fused step for all instances at once (a persistent grid
+ * striding over every instance's tiles).  Admission and retirement only rewrite a device
+ * table, never the graph.  Every instance's result is bit-identical to running it alone
+ * with lbcg_step (same per-site code).  The batch works on the stream given at creation;
+ * the instances' own streams are not used while they are in the batch.  A context must
+ * not be stepped by itself while it is in a batch.  The batch owns small device tables
+ * (slot table, work lists) and a pinned host copy of the slot table. */
+typedef struct lbcg_batch lbcg_batch;
+
+/* max_instances in 1..4096. */
+int lbcg_batch_create(int lattice, int precision, int max_instances, void* stream, lbcg_batch** out);
+void lbcg_batch_destroy(lbcg_batch* batch);
+/* Add a ready context (bound state, geometry, fields) that is to run `steps` more steps;
+ * *slot receives its slot.  LBCG_ERR_CAPACITY when the batch is full. */
+int lbcg_batch_add(lbcg_batch* batch, lbcg_ctx* ctx, long long steps, int* slot);
+/* Remove an instance (finished or not); waits for the batch's stream first. */
+int lbcg_batch_remove(lbcg_batch* batch, int slot);
+/* Steps an instance still has to run, or -1 for an empty slot. */
+long long lbcg_batch_remaining(const lbcg_batch* batch, int slot);
+/* Advance every instance by min(max_steps, its remaining steps); asynchronous. */
+int lbcg_batch_step(lbcg_batch* batch, long long max_steps);
+/* Wait for the batch's work, then report (once each) the slots that have no steps left. */
+int lbcg_batch_poll(lbcg_batch* batch, int* done_slots, int cap, int* ndone);
+/* Message of the calling thread's last failed batch call. */
+const char* lbcg_batch_last_error(void);
+
 /* Kernel timing: when enabled, CUDA events bracket every launch of the fused step
  * kernel on the context's stream; lbcg_kernel_time returns the summed duration in
  * milliseconds and the number of launches since the last reset (synchronises). */
@@ -242,7 +273,8 @@ int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
  * rows: sites per warp along the marching axis (D2Q9: y rows per warp strip;
  * D3Q19: z planes per block); block_rows: D3Q19 warps per block along y (3..16);
  * variant: 0 default, 1 keep the next row/plane's populations in registers,
- * 2 re-read them when colliding.  Results are bit-identical across shapes and
+ * 2 re-read them when colliding, 3 pipelined (collide row/plane k-2 while the loads
+ * of k are in flight).  Results are bit-identical across shapes and
  * variants; only speed changes.  Drops captured step graphs. */
 int lbcg_set_launch(lbcg_ctx* ctx, int rows, int block_rows, int variant);
 

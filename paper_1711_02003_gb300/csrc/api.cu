@@ -121,28 +121,28 @@ namespace lbcg {
 
 size_t storage_size(int precision) { return elem_size(precision); }
 
-void fill_kparams(lbcg_ctx* c)
+KParams make_kparams(const lbcg_params& p, const int dims[3], size_t np, int rows_req, int block_rows)
 {
-    KParams& k = c->kp;
+    KParams k;
     std::memset(&k, 0, sizeof(k));
-    k.nx = c->dims[0];
-    k.ny = c->dims[1];
-    k.nz = c->dims[2];
-    for (int a = 0; a < 3; ++a) k.per[a] = c->p.periodic[a] ? 1 : 0;
-    if (c->p.lattice == LBCG_D2Q9) k.per[2] = 1;
-    k.np = c->np;
-    k.collision = c->p.collision;
-    k.lattice = c->p.lattice;
-    k.alpha_r = c->p.alpha_r;
-    k.alpha_b = c->p.alpha_b;
-    fill_phys(k.pf, c->p, c->p.lattice);
-    fill_phys(k.pd, c->p, c->p.lattice);
+    k.nx = dims[0];
+    k.ny = dims[1];
+    k.nz = dims[2];
+    for (int a = 0; a < 3; ++a) k.per[a] = p.periodic[a] ? 1 : 0;
+    if (p.lattice == LBCG_D2Q9) k.per[2] = 1;
+    k.np = np;
+    k.collision = p.collision;
+    k.lattice = p.lattice;
+    k.alpha_r = p.alpha_r;
+    k.alpha_b = p.alpha_b;
+    fill_phys(k.pf, p, p.lattice);
+    fill_phys(k.pd, p, p.lattice);
     const int sms = 152;
-    if (c->p.lattice == LBCG_D2Q9) {
+    if (p.lattice == LBCG_D2Q9) {
         // strips of 30 x rows sites per warp; rows trade the ring re-reads (2/rows) against
         // enough warps for about four waves of 24 resident warps per SM (measured best: 16-32)
         k.nsx = (k.nx + 29) / 30;
-        int rows = c->rows;
+        int rows = rows_req;
         if (rows <= 0) {
             const long long target = (long long)sms * 24 * 4;
             long long r = ((long long)k.nsx * k.ny) / target;
@@ -153,14 +153,20 @@ void fill_kparams(lbcg_ctx* c)
         k.nsz = 1;
     } else {
         // blocks of 32 x 8 threads (two resident per SM) marching 8 z-planes (measured best)
-        const int wy = c->block_rows > 2 ? c->block_rows : 8;
-        c->block_rows = wy;
+        const int wy = block_rows > 2 ? block_rows : 8;
         k.nsx = (k.nx + 29) / 30;
         k.nsy = (k.ny + (wy - 2) - 1) / (wy - 2);
-        const int rows = c->rows > 0 ? c->rows : 8;
+        const int rows = rows_req > 0 ? rows_req : 8;
         k.rows = std::min(rows, k.nz);
         k.nsz = (k.nz + k.rows - 1) / k.rows;
     }
+    return k;
+}
+
+void fill_kparams(lbcg_ctx* c)
+{
+    if (c->p.lattice != LBCG_D2Q9 && c->block_rows <= 2) c->block_rows = 8;
+    c->kp = make_kparams(c->p, c->dims, c->np, c->rows, c->block_rows);
 }
 
 }  // namespace lbcg
@@ -243,6 +249,7 @@ void lbcg_destroy(lbcg_ctx* c)
     drop_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     free_tables(c);
+    cudaFree(c->d_scratch);
     cudaFree(c->d_partials);
     cudaFree(c->d_result);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -412,6 +419,33 @@ int lbcg_set_geometry(lbcg_ctx* c, const uint8_t* mask, const lbcg_port* ports, 
     return LBCG_OK;
 }
 
+// device scratch of at least `bytes` for staging and read-back (never the state buffers,
+// so the stored state stays defined at every site)
+static int scratch(lbcg_ctx* c, size_t bytes, void** out)
+{
+    if (c->scratch_bytes < bytes) {
+        if (c->d_scratch) {
+            cudaError_t e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "scratch sync");
+            cudaFree(c->d_scratch);
+            c->d_scratch = nullptr;
+            c->scratch_bytes = 0;
+        }
+        if (cudaMalloc(&c->d_scratch, bytes) != cudaSuccess) return fail(LBCG_ERR_NOMEM, "scratch allocation failed");
+        c->scratch_bytes = bytes;
+    }
+    *out = c->d_scratch;
+    return LBCG_OK;
+}
+
+// after A has been (re)initialised: give B the same contents, so both buffers hold a
+// defined value at every site (walls stay zero, ghosts are refilled each step)
+static int mirror_state(lbcg_ctx* c)
+{
+    LBCG_CUDA(cudaMemcpyAsync(c->B, c->A, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream), "mirror state");
+    return LBCG_OK;
+}
+
 static int need(lbcg_ctx* c, bool fields)
 {
     if (!c) return fail(LBCG_ERR_ARG, "null context");
@@ -427,6 +461,8 @@ int lbcg_init_fields_device(lbcg_ctx* c, const double* rr, const double* rb, con
     if (st) return st;
     if (!rr || !rb) return fail(LBCG_ERR_ARG, "null density field");
     LBCG_CUDA(launch_init(c, rr, rb, u, c->A), "init kernel");
+    st = mirror_state(c);
+    if (st) return st;
     c->fields = true;
     c->step = 0;
     return LBCG_OK;
@@ -437,13 +473,18 @@ int lbcg_init_fields(lbcg_ctx* c, const double* rr, const double* rb, const doub
     int st = need(c, false);
     if (st) return st;
     if (!rr || !rb) return fail(LBCG_ERR_ARG, "null density field");
-    // stage in the inactive buffer: rho_r | rho_b | u
-    double* stg = (double*)c->B;
+    // staging: rho_r | rho_b | u
     const size_t n = (size_t)c->n;
+    void* sp = nullptr;
+    st = scratch(c, n * 8 * (2 + c->D), &sp);
+    if (st) return st;
+    double* stg = (double*)sp;
     LBCG_CUDA(cudaMemcpyAsync(stg, rr, n * 8, cudaMemcpyHostToDevice, c->stream), "copy rho_r");
     LBCG_CUDA(cudaMemcpyAsync(stg + n, rb, n * 8, cudaMemcpyHostToDevice, c->stream), "copy rho_b");
     if (u) LBCG_CUDA(cudaMemcpyAsync(stg + 2 * n, u, n * 8 * c->D, cudaMemcpyHostToDevice, c->stream), "copy u");
     LBCG_CUDA(launch_init(c, stg, stg + n, u ? stg + 2 * n : nullptr, c->A), "init kernel");
+    st = mirror_state(c);
+    if (st) return st;
     LBCG_CUDA(cudaStreamSynchronize(c->stream), "init sync");
     c->fields = true;
     c->step = 0;
@@ -595,8 +636,11 @@ int lbcg_get_fields(lbcg_ctx* c, double* rr, double* rb, double* u)
     int st = need(c, true);
     if (st) return st;
     if (!rr || !rb || !u) return fail(LBCG_ERR_ARG, "null output");
-    double* stg = (double*)c->B;
     const size_t n = (size_t)c->n;
+    void* sp = nullptr;
+    st = scratch(c, n * 8 * (2 + c->D), &sp);
+    if (st) return st;
+    double* stg = (double*)sp;
     LBCG_CUDA(launch_fields(c, c->A, stg, stg + n, stg + 2 * n), "fields kernel");
     LBCG_CUDA(cudaMemcpyAsync(rr, stg, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy rho_r");
     LBCG_CUDA(cudaMemcpyAsync(rb, stg + n, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy rho_b");
@@ -610,8 +654,11 @@ int lbcg_get_populations(lbcg_ctx* c, double* f)
     int st = need(c, true);
     if (st) return st;
     if (!f) return fail(LBCG_ERR_ARG, "null output");
-    double* stg = (double*)c->B;
     const size_t n = (size_t)c->n;
+    void* sp = nullptr;
+    st = scratch(c, n * 8, &sp);
+    if (st) return st;
+    double* stg = (double*)sp;
     for (int k = 0; k < 2; ++k)
         for (int i = 0; i < c->Q; ++i) {
             LBCG_CUDA(launch_pop_plane_to_f64(c, c->A, k, i, stg), "population kernel");
@@ -628,8 +675,11 @@ int lbcg_set_populations(lbcg_ctx* c, const double* f)
     int st = need(c, false);
     if (st) return st;
     if (!f) return fail(LBCG_ERR_ARG, "null input");
-    double* stg = (double*)c->B;
     const size_t n = (size_t)c->n;
+    void* sp = nullptr;
+    st = scratch(c, n * 16, &sp);
+    if (st) return st;
+    double* stg = (double*)sp;
     for (int i = 0; i < c->Q; ++i) {
         LBCG_CUDA(cudaMemcpyAsync(stg, f + (size_t)i * n, n * 8, cudaMemcpyHostToDevice, c->stream), "copy red");
         LBCG_CUDA(cudaMemcpyAsync(stg + n, f + ((size_t)c->Q + i) * n, n * 8, cudaMemcpyHostToDevice, c->stream),
@@ -637,6 +687,9 @@ int lbcg_set_populations(lbcg_ctx* c, const double* f)
         LBCG_CUDA(launch_pops_from_f64(c, stg, c->A, i), "population kernel");
         LBCG_CUDA(cudaStreamSynchronize(c->stream), "populations sync");
     }
+    st = mirror_state(c);
+    if (st) return st;
+    LBCG_CUDA(cudaStreamSynchronize(c->stream), "populations sync");
     c->fields = true;
     return LBCG_OK;
 }
@@ -688,8 +741,11 @@ int lbcg_label(lbcg_ctx* c, int32_t* labels, int64_t* counts, double* volumes, i
     if (st) return st;
     if (!labels || !n_drops || cap < 0) return fail(LBCG_ERR_ARG, "null output");
     const size_t n = (size_t)c->n;
-    // scratch in the inactive buffer: half[n] doubles | labels[n] ints | flag
-    double* half = (double*)c->B;
+    // scratch: half[n] doubles | labels[n] ints | flag
+    void* sp = nullptr;
+    st = scratch(c, n * 12 + 16, &sp);
+    if (st) return st;
+    double* half = (double*)sp;
     int32_t* L = (int32_t*)(half + n);
     int* flag = (int*)(L + n + (n & 1));
     LBCG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->stream), "clear flag");
@@ -756,8 +812,8 @@ int lbcg_set_launch(lbcg_ctx* c, int rows, int block_rows, int variant)
 {
     if (!c) return fail(LBCG_ERR_ARG, "null context");
     if (rows < 0 || block_rows < 0 || (block_rows > 0 && (block_rows < 3 || block_rows > 8)) || variant < 0 ||
-        variant > 2)
-        return fail(LBCG_ERR_ARG, "launch shape out of range (block_rows in 3..16, variant in 0..2)");
+        variant > 3)
+        return fail(LBCG_ERR_ARG, "launch shape out of range (block_rows in 3..8, variant in 0..3)");
     c->rows = rows;
     c->block_rows = block_rows;
     c->variant = variant;

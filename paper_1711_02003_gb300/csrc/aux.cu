@@ -2,7 +2,7 @@
 // field and population read-back, FP64 observable reductions and droplet labelling
 // (arXiv:1711.02003: Eqs. 2-3 moments, Eq. 6 equilibrium, Eq. 8 pressure; the
 // observables follow the resting-droplet and droplet-size analyses of Secs. IV A-B).
-#include "lbcg_device.cuh"
+#include "obs_kernels.cuh"
 
 namespace lbcg {
 
@@ -65,63 +65,93 @@ __device__ __forceinline__ void store_rb(const KParams& P, typename Store<PREC>:
 //   velocity:      f^k = f^{k,eq}(chi^k rho', u_port) + chi^k (f(x') - f^eq(x'))
 //   pressure:      f^k = f^{k,eq}(rho_port rho'^k / rho', u') + f^k(x') - f^{k,eq}(x')
 //   zero-gradient: f^k = f^k(x')
-// Arithmetic in FP64 (a few thousand sites per step).
+// One warp per ghost: lane i < Q handles direction i; the moments of x' are warp sums.
+// Arithmetic in FP64 whatever the storage (only the few thousand port sites; f - f^eq of
+// plain populations would lose the deviation format's precision in FP32).
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 template <int LAT, int PREC>
-__global__ void k_fill_ports(const KParams P, typename Store<PREC>::S* __restrict__ a, const int* __restrict__ tab,
-                             const double* __restrict__ gu, int ng)
+__device__ __forceinline__ void fill_one(const KParams& P, typename Store<PREC>::S* __restrict__ a,
+                                         const int* __restrict__ tab, const double* __restrict__ gu, int ng, int t)
 {
     using L = Lat<LAT>;
+    using SP = Store<PREC>;
+    using T = double;
     constexpr int Q = L::Q;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ng) return;
+    const int lane = threadIdx.x & 31;
+    const Phys<double>& ph = P.pd;
     const size_t g = (size_t)tab[t];
     const size_t xp = (size_t)tab[ng + t];
     const int kind = tab[3 * ng + t];
-    double fr[Q], fb[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) load_rb<LAT, PREC>(P, a, i, xp, fr[i], fb[i]);
+    const bool act = lane < Q;
+    const int i = act ? lane : 0;
     if (kind == LBCG_PORT_ZERO_GRADIENT) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) store_rb<LAT, PREC>(P, a, i, g, fr[i], fb[i]);
+        if (act) {
+            typename SP::T r, gg;
+            const Phys<typename SP::T>& pt = phys<typename SP::T>(P);
+            SP::load(a, (size_t)i * P.np + xp, (size_t)(Q + i) * P.np + xp, pt, L::cls(i), r, gg);
+            SP::store(a, (size_t)i * P.np + g, (size_t)(Q + i) * P.np + g, pt, L::cls(i), r, gg);
+        }
         return;
     }
-    double rr = 0, rb = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        rr += fr[i];
-        rb += fb[i];
-        const double f = fr[i] + fb[i];
-        jx += L::cx(i) * f;
-        jy += L::cy(i) * f;
-        jz += L::cz(i) * f;
-    }
-    const double rho = rr + rb;
-    const double ux = jx / rho, uy = jy / rho, uz = jz / rho;
-    const double(&phR)[3] = P.pd.phiR;
-    const double(&phB)[3] = P.pd.phiB;
+    T fr = 0, fb = 0;
+    if (act) load_rb<LAT, PREC>(P, a, i, xp, fr, fb);
+    const T f = fr + fb;
+    const T rr = warp_sum(fr), rb = warp_sum(fb);
+    const T jx = warp_sum(f * (T)L::cx(i)), jy = warp_sum(f * (T)L::cy(i)), jz = warp_sum(f * (T)L::cz(i));
+    if (!act) return;
+    const T rho = rr + rb;
+    const T ux = jx / rho, uy = jy / rho, uz = jz / rho;
+    T gr, gb;
     if (kind == LBCG_PORT_VELOCITY) {
-        const double vx = gu[t], vy = gu[ng + t], vz = gu[2 * ng + t];
-        const double psi = gu[4 * ng + t];
-        const double xr = (1.0 + psi) / 2.0, xb = (1.0 - psi) / 2.0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const double fneq = (fr[i] + fb[i]) - (feq_comp<LAT, double>(phR, rr, ux, uy, uz, i) +
-                                                   feq_comp<LAT, double>(phB, rb, ux, uy, uz, i));
-            const double gr = feq_comp<LAT, double>(phR, xr * rho, vx, vy, vz, i) + xr * fneq;
-            const double gb = feq_comp<LAT, double>(phB, xb * rho, vx, vy, vz, i) + xb * fneq;
-            store_rb<LAT, PREC>(P, a, i, g, gr, gb);
-        }
+        const T vx = gu[t], vy = gu[ng + t], vz = gu[2 * ng + t];
+        const T psi = gu[4 * ng + t];
+        const T xr = (1.0 + psi) / 2.0, xb = (1.0 - psi) / 2.0;
+        const T fneq = f - (feq_comp<LAT, T>(ph.phiR, rr, ux, uy, uz, i) + feq_comp<LAT, T>(ph.phiB, rb, ux, uy, uz, i));
+        gr = feq_comp<LAT, T>(ph.phiR, xr * rho, vx, vy, vz, i) + xr * fneq;
+        gb = feq_comp<LAT, T>(ph.phiB, xb * rho, vx, vy, vz, i) + xb * fneq;
     } else {
-        const double rho_out = gu[3 * ng + t];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const double gr = feq_comp<LAT, double>(phR, rho_out * rr / rho, ux, uy, uz, i) +
-                              (fr[i] - feq_comp<LAT, double>(phR, rr, ux, uy, uz, i));
-            const double gb = feq_comp<LAT, double>(phB, rho_out * rb / rho, ux, uy, uz, i) +
-                              (fb[i] - feq_comp<LAT, double>(phB, rb, ux, uy, uz, i));
-            store_rb<LAT, PREC>(P, a, i, g, gr, gb);
-        }
+        const T rho_out = gu[3 * ng + t];
+        gr = feq_comp<LAT, T>(ph.phiR, rho_out * rr / rho, ux, uy, uz, i) +
+             (fr - feq_comp<LAT, T>(ph.phiR, rr, ux, uy, uz, i));
+        gb = feq_comp<LAT, T>(ph.phiB, rho_out * rb / rho, ux, uy, uz, i) +
+             (fb - feq_comp<LAT, T>(ph.phiB, rb, ux, uy, uz, i));
     }
+    store_rb<LAT, PREC>(P, a, i, g, gr, gb);
+}
+
+template <int LAT, int PREC>
+__global__ void __launch_bounds__(128) k_fill_ports(const KParams P, typename Store<PREC>::S* __restrict__ a,
+                                                    const int* __restrict__ tab, const double* __restrict__ gu,
+                                                    int ng)
+{
+    const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (t >= ng) return;  // warp-uniform
+    fill_one<LAT, PREC>(P, a, tab, gu, ng, t);
+}
+
+// batched refill: work item (slot, first ghost, count <= 4); warp w of the block takes one
+// ghost; node k refills the source buffer of step k of instances with steps > k
+template <int LAT, int PREC>
+__global__ void __launch_bounds__(128) k_batch_fill(const BatchSlot* __restrict__ slots,
+                                                    const BatchItem* __restrict__ items,
+                                                    const int* __restrict__ nitems, int k)
+{
+    const int w = blockIdx.x;
+    if (w >= *nitems) return;
+    const BatchItem it = items[w];
+    const BatchSlot& sl = slots[it.slot];
+    if (k >= sl.steps) return;
+    const int wib = threadIdx.x >> 5;
+    if (wib >= it.y) return;
+    typename Store<PREC>::S* src = (typename Store<PREC>::S*)((k & 1) ? sl.b : sl.a);
+    fill_one<LAT, PREC>(sl.kp, src, sl.ghost, sl.ghost_u, sl.nghost, it.x + wib);
 }
 
 // ---------------------------------------------------------------- initial state
@@ -156,29 +186,18 @@ __global__ void k_fields(const KParams P, const typename Store<PREC>::S* __restr
                          double* __restrict__ orb, double* __restrict__ ou)
 {
     using L = Lat<LAT>;
+    using T = typename Store<PREC>::T;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
          s += (long long)gridDim.x * blockDim.x) {
         const bool fluid = link == nullptr || ((link[s] >> kTypeShift) & 3u) == kTypeFluid;
-        double rr = 0, rb = 0, jx = 0, jy = 0, jz = 0;
-        if (fluid) {
-#pragma unroll
-            for (int i = 0; i < L::Q; ++i) {
-                double fr, fb;
-                load_rb<LAT, PREC>(P, a, i, (size_t)s, fr, fb);
-                rr += fr;
-                rb += fb;
-                const double f = fr + fb;
-                jx += L::cx(i) * f;
-                jy += L::cy(i) * f;
-                jz += L::cz(i) * f;
-            }
-        }
-        const double rho = rr + rb;
-        orr[s] = rr;
-        orb[s] = rb;
-        ou[s] = rho > 0 ? jx / rho : 0.0;
-        ou[n + s] = rho > 0 ? jy / rho : 0.0;
-        if (L::D == 3) ou[2 * n + s] = rho > 0 ? jz / rho : 0.0;
+        T rr = 0, rb = 0, rho = 0, j[3] = {0, 0, 0};
+        if (fluid) obs_site<LAT, PREC>(P, a, (size_t)s, rr, rb, rho, j);
+        const bool ok = fluid && rho > T(0);
+        orr[s] = fluid ? (double)rr : 0.0;
+        orb[s] = fluid ? (double)rb : 0.0;
+        ou[s] = ok ? (double)(j[0] / rho) : 0.0;
+        ou[n + s] = ok ? (double)(j[1] / rho) : 0.0;
+        if (L::D == 3) ou[2 * n + s] = ok ? (double)(j[2] / rho) : 0.0;
     }
 }
 
@@ -203,162 +222,6 @@ __global__ void k_dir_from_f64(const KParams P, const double* __restrict__ fr, c
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
          s += (long long)gridDim.x * blockDim.x)
         store_rb<LAT, PREC>(P, a, i, (size_t)s, fr[s], fb[s]);
-}
-
-// ------------------------------------------------------------------ reductions
-// Deterministic two-level FP64 reductions: a fixed grid of kMaxPartials-or-fewer
-// blocks, each thread strides over sites in a fixed order, warp shuffles then
-// shared memory inside a block, per-block partials reduced by one block in index
-// order.  Results do not depend on timing.
-
-template <int NS>
-__device__ __forceinline__ void block_reduce(double (&v)[NS], const bool (&is_max)[NS], double* out_row)
-{
-    __shared__ double sh[32][NS];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NS; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double t = __shfl_xor_sync(0xffffffffu, v[k], o);
-            v[k] = is_max[k] ? fmax(v[k], t) : v[k] + t;
-        }
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NS; ++k) sh[warp][k] = v[k];
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-            double t = lane < nw ? sh[lane][k] : (is_max[k] ? 0.0 : 0.0);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const double q = __shfl_xor_sync(0xffffffffu, t, o);
-                t = is_max[k] ? fmax(t, q) : t + q;
-            }
-            if (lane == 0) out_row[k] = t;
-        }
-    }
-}
-
-constexpr int kS1 = 8;  // mass_r, mass_b, mom x, y, z, amount, umax, nonfinite
-constexpr int kS2 = 4;  // p_in sum, n_in, p_out sum, n_out
-
-template <int LAT, int PREC>
-__global__ void __launch_bounds__(256) k_obs_pass1(const KParams P, const typename Store<PREC>::S* __restrict__ a,
-                                                   const uint32_t* __restrict__ link, long long n,
-                                                   double* __restrict__ partials)
-{
-    using L = Lat<LAT>;
-    double v[kS1] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const bool mx[kS1] = {false, false, false, false, false, false, true, false};
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
-         s += (long long)gridDim.x * blockDim.x) {
-        if (link && ((link[s] >> kTypeShift) & 3u) != kTypeFluid) continue;
-        double rr = 0, rb = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-            double fr, fb;
-            load_rb<LAT, PREC>(P, a, i, (size_t)s, fr, fb);
-            rr += fr;
-            rb += fb;
-            const double f = fr + fb;
-            jx += L::cx(i) * f;
-            jy += L::cy(i) * f;
-            jz += L::cz(i) * f;
-        }
-        const double rho = rr + rb;
-        if (!(rho > 0.0) || !isfinite(rho)) {
-            v[7] += 1.0;
-            continue;
-        }
-        v[0] += rr;
-        v[1] += rb;
-        v[2] += jx;
-        v[3] += jy;
-        v[4] += jz;
-        v[5] += (1.0 + (rr - rb) / rho) / 2.0;
-        v[6] = fmax(v[6], sqrt(jx * jx + jy * jy + jz * jz) / rho);
-    }
-    block_reduce<kS1>(v, mx, partials + (size_t)blockIdx.x * kObsSlots);
-}
-
-template <int LAT, int PREC>
-__global__ void __launch_bounds__(256) k_obs_pass2(const KParams P, const typename Store<PREC>::S* __restrict__ a,
-                                                   const uint32_t* __restrict__ link, long long n, double cx,
-                                                   double cy, double cz, double kpr, double kpb,
-                                                   const double* __restrict__ res, double* __restrict__ partials)
-{
-    using L = Lat<LAT>;
-    const double r_in = res[9], r_out = res[10];
-    double v[kS2] = {0, 0, 0, 0};
-    const bool mx[kS2] = {false, false, false, false};
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
-         s += (long long)gridDim.x * blockDim.x) {
-        if (link && ((link[s] >> kTypeShift) & 3u) != kTypeFluid) continue;
-        int x, y, z;
-        coords(s, P.nx, P.ny, x, y, z);
-        double d2 = 0.0;
-        {
-            double dd = fabs((double)x - cx);
-            if (P.per[0] && P.nx - dd < dd) dd = P.nx - dd;
-            d2 += dd * dd;
-            dd = fabs((double)y - cy);
-            if (P.per[1] && P.ny - dd < dd) dd = P.ny - dd;
-            d2 += dd * dd;
-            if (L::D == 3) {
-                dd = fabs((double)z - cz);
-                if (P.per[2] && P.nz - dd < dd) dd = P.nz - dd;
-                d2 += dd * dd;
-            }
-        }
-        const double r = sqrt(d2);
-        if (r >= r_in && r <= r_out) continue;
-        double rr = 0, rb = 0;
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) {
-            double fr, fb;
-            load_rb<LAT, PREC>(P, a, i, (size_t)s, fr, fb);
-            rr += fr;
-            rb += fb;
-        }
-        const double p = kpr * rr + kpb * rb;
-        if (r < r_in) {
-            v[0] += p;
-            v[1] += 1.0;
-        } else {
-            v[2] += p;
-            v[3] += 1.0;
-        }
-    }
-    block_reduce<kS2>(v, mx, partials + (size_t)blockIdx.x * kObsSlots);
-}
-
-// one block: reduce nb partial rows of ns slots in block-index order into res[off..]
-__global__ void k_obs_final(const double* __restrict__ partials, int nb, int ns, unsigned maxmask, int off,
-                            double* __restrict__ res, int dim, double r_in, double r_out)
-{
-    // thread k reduces slot k sequentially over blocks: fixed order
-    const int k = threadIdx.x;
-    if (k < ns) {
-        const bool is_max = (maxmask >> k) & 1u;
-        double t = 0.0;
-        for (int b = 0; b < nb; ++b) {
-            const double q = partials[(size_t)b * kObsSlots + k];
-            t = is_max ? fmax(t, q) : t + q;
-        }
-        res[off + k] = t;
-    }
-    __syncthreads();
-    if (off == 0 && k == 0) {
-        const double amount = res[5];
-        const double pi = 3.14159265358979323846;
-        const double reff = dim == 2 ? sqrt(amount / pi) : cbrt(3.0 * amount / (4.0 * pi));
-        res[8] = reff;
-        res[9] = r_in < 0.0 ? reff / 2.0 : r_in;
-        res[10] = r_out < 0.0 ? reff + 5.0 : r_out;
-    }
 }
 
 // ------------------------------------------------------------------- labelling
@@ -486,11 +349,31 @@ using SOf = typename Store<PREC>::S;
 cudaError_t launch_fill_ports(lbcg_ctx* c, void* a)
 {
     if (c->nghost == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((c->nghost + 127) / 128);
+    const unsigned blocks = (unsigned)((c->nghost + 3) / 4);  // 4 warps (ghosts) per block
 #define F_(LAT, PREC) \
     k_fill_ports<LAT, PREC><<<blocks, 128, 0, c->stream>>>(c->kp, (SOf<PREC>*)a, c->d_ghost, c->d_ghost_u, c->nghost)
     LBCG_DISPATCH(c, F_);
 #undef F_
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_fill(int lattice, int precision, const BatchSlot* slots, const BatchItem* items,
+                              const int* nitems, int cap, int k, cudaStream_t st)
+{
+    if (cap <= 0) return cudaSuccess;
+#define BF_(LAT, PREC) k_batch_fill<LAT, PREC><<<(unsigned)cap, 128, 0, st>>>(slots, items, nitems, k)
+    if (lattice == LBCG_D2Q9) {
+        if (precision == LBCG_FP64) BF_(0, LBCG_FP64);
+        else if (precision == LBCG_FP32) BF_(0, LBCG_FP32);
+        else if (precision == LBCG_FP32_DEV) BF_(0, LBCG_FP32_DEV);
+        else BF_(0, LBCG_FP16_SCALED);
+    } else {
+        if (precision == LBCG_FP64) BF_(1, LBCG_FP64);
+        else if (precision == LBCG_FP32) BF_(1, LBCG_FP32);
+        else if (precision == LBCG_FP32_DEV) BF_(1, LBCG_FP32_DEV);
+        else BF_(1, LBCG_FP16_SCALED);
+    }
+#undef BF_
     return cudaGetLastError();
 }
 
@@ -542,24 +425,8 @@ cudaError_t launch_observables(lbcg_ctx* c, const void* a, const double centre[3
     long long b = (c->n + 255) / 256;
     if (b > kMaxPartials) b = kMaxPartials;
     if (b < 1) b = 1;
-    const unsigned nb = (unsigned)b;
-    const uint32_t* lk = c->any_link ? c->d_link : nullptr;
-    const int dim = c->D;
-    const double ar = c->p.alpha_r, ab = c->p.alpha_b;
-    const double kpr = dim == 2 ? 3.0 * (1.0 - ar) / 5.0 : (1.0 - ar) / 2.0;
-    const double kpb = dim == 2 ? 3.0 * (1.0 - ab) / 5.0 : (1.0 - ab) / 2.0;
-#define F_(LAT, PREC) \
-    k_obs_pass1<LAT, PREC><<<nb, 256, 0, c->stream>>>(c->kp, (const SOf<PREC>*)a, lk, c->n, d_partials)
-    LBCG_DISPATCH(c, F_);
-#undef F_
-    k_obs_final<<<1, 32, 0, c->stream>>>(d_partials, (int)nb, kS1, 1u << 6, 0, d_result, dim, r_in, r_out);
-#define F_(LAT, PREC)                                                                                         \
-    k_obs_pass2<LAT, PREC><<<nb, 256, 0, c->stream>>>(c->kp, (const SOf<PREC>*)a, lk, c->n, centre[0],      \
-                                                       centre[1], centre[2], kpr, kpb, d_result, d_partials)
-    LBCG_DISPATCH(c, F_);
-#undef F_
-    k_obs_final<<<1, 32, 0, c->stream>>>(d_partials, (int)nb, kS2, 0u, 11, d_result, dim, r_in, r_out);
-    return cudaGetLastError();
+    return run_observables(*c, a, FluidLink{c->any_link ? c->d_link : nullptr}, centre, r_in, r_out, (int)b,
+                           d_partials, d_result, c->stream);
 }
 
 cudaError_t launch_label(lbcg_ctx* c, const void* a, int32_t* L, double* half, int* d_flag)

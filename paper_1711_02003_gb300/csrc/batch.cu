@@ -1,0 +1,301 @@
+// batch.cu -- many independent instances advanced together (lbcg_batch_*).
+//
+// A batch holds up to max_instances contexts of one lattice and storage precision.  Each
+// lbcg_batch_step chunk replays one captured CUDA graph of kBatchGraphSteps nodes; node k
+// refills the port ghosts and runs the batched fused step for every instance with more
+// than k steps left in the chunk.  Which instances take part, their buffers and step
+// counts live in a device table the host rewrites before each replay, so admitting or
+// retiring an instance never re-captures the graph (only a larger work list does).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbcg_device.cuh"
+
+using namespace lbcg;
+
+namespace {
+constexpr int kBatchGraphSteps = 32;
+constexpr int kBatch2DRows = 16;
+}  // namespace
+
+struct lbcg_batch {
+    int lattice = 0, precision = 0, max_slots = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<lbcg_ctx*> ctx;           // nullptr = free slot
+    std::vector<long long> remaining;     // steps still to run
+    std::vector<char> reported;           // completion already returned by poll
+    std::vector<KParams> kp;              // per-slot launch-shaped parameters
+    BatchSlot* h_slots = nullptr;         // pinned
+    BatchSlot* d_slots = nullptr;
+    std::vector<BatchItem> h_items, h_fill;
+    BatchItem* d_items = nullptr;
+    BatchItem* d_fill = nullptr;
+    int* d_counts = nullptr;              // [0] step items, [1] fill items
+    int items_cap = 0, fill_cap = 0;
+    bool dirty = true;                    // membership changed: rebuild work lists
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_berr;
+
+int bfail(int code, const std::string& m)
+{
+    g_berr = m;
+    return code;
+}
+
+void drop_graph(lbcg_batch* b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+// rebuild the work lists of the occupied slots; grow device capacity if needed
+int rebuild(lbcg_batch* b)
+{
+    b->h_items.clear();
+    b->h_fill.clear();
+    for (int s = 0; s < b->max_slots; ++s) {
+        if (!b->ctx[s]) continue;
+        const KParams& k = b->kp[s];
+        if (b->lattice == LBCG_D2Q9) {
+            const int strips = k.nsx * k.nsy;
+            for (int f = 0; f < strips; f += 8) b->h_items.push_back({s, f, std::min(8, strips - f), 0});
+        } else {
+            for (int z = 0; z < k.nsz; ++z)
+                for (int y = 0; y < k.nsy; ++y)
+                    for (int x = 0; x < k.nsx; ++x) b->h_items.push_back({s, x, y, z});
+        }
+        const int ng = b->ctx[s]->nghost;
+        for (int f = 0; f < ng; f += 4) b->h_fill.push_back({s, f, std::min(4, ng - f), 0});
+    }
+    const int ni = (int)b->h_items.size(), nf = (int)b->h_fill.size();
+    if (ni > b->items_cap || nf > b->fill_cap) {
+        drop_graph(b);
+        if (ni > b->items_cap) {
+            cudaFree(b->d_items);
+            b->items_cap = std::max(ni, 2 * b->items_cap);
+            if (cudaMalloc(&b->d_items, sizeof(BatchItem) * b->items_cap) != cudaSuccess)
+                return bfail(LBCG_ERR_NOMEM, "batch work list allocation failed");
+        }
+        if (nf > b->fill_cap) {
+            cudaFree(b->d_fill);
+            b->fill_cap = std::max(nf, std::max(64, 2 * b->fill_cap));
+            if (cudaMalloc(&b->d_fill, sizeof(BatchItem) * b->fill_cap) != cudaSuccess)
+                return bfail(LBCG_ERR_NOMEM, "batch refill list allocation failed");
+        }
+    }
+    int counts[2] = {ni, nf};
+    cudaError_t e = cudaSuccess;
+    if (ni) e = cudaMemcpyAsync(b->d_items, b->h_items.data(), sizeof(BatchItem) * ni, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && nf)
+        e = cudaMemcpyAsync(b->d_fill, b->h_fill.data(), sizeof(BatchItem) * nf, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(LBCG_ERR_CUDA, std::string("batch work lists: ") + cudaGetErrorString(e));
+    b->dirty = false;
+    return LBCG_OK;
+}
+
+int capture(lbcg_batch* b)
+{
+    if (b->graph) return LBCG_OK;
+    if (!b->cap_stream && cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bfail(LBCG_ERR_CUDA, "batch capture stream");
+    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(LBCG_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < kBatchGraphSteps && le == cudaSuccess; ++k) {
+        le = launch_batch_fill(b->lattice, b->precision, b->d_slots, b->d_fill, b->d_counts + 1, b->fill_cap, k,
+                               b->cap_stream);
+        if (le == cudaSuccess)
+            le = launch_batch_step(b->lattice, b->precision, b->d_slots, b->d_items, b->d_counts, k, b->cap_stream);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(LBCG_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(le != cudaSuccess ? le : e));
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(LBCG_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    return LBCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbcg_batch_last_error(void) { return g_berr.c_str(); }
+
+int lbcg_batch_create(int lattice, int precision, int max_instances, void* stream, lbcg_batch** out)
+{
+    if (!out) return bfail(LBCG_ERR_ARG, "null output");
+    *out = nullptr;
+    if (lattice != LBCG_D2Q9 && lattice != LBCG_D3Q19) return bfail(LBCG_ERR_ARG, "unknown lattice");
+    if (precision < LBCG_FP64 || precision > LBCG_FP16_SCALED) return bfail(LBCG_ERR_ARG, "unknown precision");
+    if (max_instances < 1 || max_instances > 4096) return bfail(LBCG_ERR_ARG, "max_instances must be 1..4096");
+    lbcg_batch* b = new (std::nothrow) lbcg_batch();
+    if (!b) return bfail(LBCG_ERR_NOMEM, "host allocation failed");
+    b->lattice = lattice;
+    b->precision = precision;
+    b->max_slots = max_instances;
+    b->stream = (cudaStream_t)stream;
+    cudaGetDevice(&b->device);
+    b->ctx.assign(max_instances, nullptr);
+    b->remaining.assign(max_instances, 0);
+    b->reported.assign(max_instances, 0);
+    b->kp.resize(max_instances);
+    bool ok = cudaMallocHost(&b->h_slots, sizeof(BatchSlot) * max_instances) == cudaSuccess &&
+              cudaMalloc(&b->d_slots, sizeof(BatchSlot) * max_instances) == cudaSuccess &&
+              cudaMalloc(&b->d_counts, 2 * sizeof(int)) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        lbcg_batch_destroy(b);
+        return bfail(LBCG_ERR_NOMEM, "batch tables allocation failed");
+    }
+    std::memset(b->h_slots, 0, sizeof(BatchSlot) * max_instances);
+    cudaMemsetAsync(b->d_slots, 0, sizeof(BatchSlot) * max_instances, b->stream);
+    cudaMemsetAsync(b->d_counts, 0, 2 * sizeof(int), b->stream);
+    *out = b;
+    return LBCG_OK;
+}
+
+void lbcg_batch_destroy(lbcg_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->done) cudaEventDestroy(b->done);
+    cudaFreeHost(b->h_slots);
+    cudaFree(b->d_slots);
+    cudaFree(b->d_items);
+    cudaFree(b->d_fill);
+    cudaFree(b->d_counts);
+    delete b;
+}
+
+int lbcg_batch_add(lbcg_batch* b, lbcg_ctx* c, long long steps, int* slot)
+{
+    if (!b || !c || !slot) return bfail(LBCG_ERR_ARG, "null argument");
+    if (steps < 0) return bfail(LBCG_ERR_ARG, "negative step count");
+    if (c->p.lattice != b->lattice || c->p.precision != b->precision)
+        return bfail(LBCG_ERR_ARG, "instance lattice/precision differs from the batch");
+    if (!c->bound || !c->geometry || !c->fields) return bfail(LBCG_ERR_STATE, "instance not ready (state, geometry, fields)");
+    if ((long long)2 * c->Q * (long long)c->np >= (1LL << 31) - 1)
+        return bfail(LBCG_ERR_CAPACITY, "instance too large for the batched kernels (2Q planes >= 2^31 elements)");
+    for (int s = 0; s < b->max_slots; ++s)
+        if (b->ctx[s] == c) return bfail(LBCG_ERR_ARG, "instance already in the batch");
+    int s = -1;
+    for (int i = 0; i < b->max_slots; ++i)
+        if (!b->ctx[i]) {
+            s = i;
+            break;
+        }
+    if (s < 0) return bfail(LBCG_ERR_CAPACITY, "batch is full");
+    b->ctx[s] = c;
+    b->remaining[s] = steps;
+    b->reported[s] = 0;
+    b->kp[s] = make_kparams(c->p, c->dims, c->np, b->lattice == LBCG_D2Q9 ? kBatch2DRows : 8, 8);
+    b->dirty = true;
+    *slot = s;
+    return LBCG_OK;
+}
+
+int lbcg_batch_remove(lbcg_batch* b, int slot)
+{
+    if (!b || slot < 0 || slot >= b->max_slots || !b->ctx[slot]) return bfail(LBCG_ERR_ARG, "no such slot");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(LBCG_ERR_CUDA, cudaGetErrorString(e));
+    b->ctx[slot] = nullptr;
+    b->remaining[slot] = 0;
+    b->dirty = true;
+    return LBCG_OK;
+}
+
+long long lbcg_batch_remaining(const lbcg_batch* b, int slot)
+{
+    if (!b || slot < 0 || slot >= b->max_slots || !b->ctx[slot]) return -1;
+    return b->remaining[slot];
+}
+
+int lbcg_batch_step(lbcg_batch* b, long long max_steps)
+{
+    if (!b) return bfail(LBCG_ERR_ARG, "null batch");
+    if (max_steps < 0) return bfail(LBCG_ERR_ARG, "negative step count");
+    long long done = 0;
+    while (done < max_steps) {
+        bool any = false;
+        for (int s = 0; s < b->max_slots; ++s)
+            if (b->ctx[s] && b->remaining[s] > 0) any = true;
+        if (!any) break;
+        if (b->dirty) {
+            int st = rebuild(b);
+            if (st) return st;
+        }
+        int st = capture(b);
+        if (st) return st;
+        // the previous replay must have consumed the pinned slot table before it is rewritten
+        cudaError_t e = cudaEventSynchronize(b->done);
+        if (e != cudaSuccess) return bfail(LBCG_ERR_CUDA, cudaGetErrorString(e));
+        const long long chunk = std::min<long long>(kBatchGraphSteps, max_steps - done);
+        for (int s = 0; s < b->max_slots; ++s) {
+            BatchSlot& h = b->h_slots[s];
+            lbcg_ctx* c = b->ctx[s];
+            if (!c) {
+                h.steps = 0;
+                continue;
+            }
+            h.kp = b->kp[s];
+            h.a = c->A;
+            h.b = c->B;
+            h.link = c->any_link ? c->d_link : nullptr;
+            h.ghost = c->d_ghost;
+            h.ghost_u = c->d_ghost_u;
+            h.nghost = c->nghost;
+            h.steps = (int)std::min<long long>(chunk, b->remaining[s]);
+        }
+        e = cudaMemcpyAsync(b->d_slots, b->h_slots, sizeof(BatchSlot) * b->max_slots, cudaMemcpyHostToDevice,
+                            b->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(b->done, b->stream);
+        if (e != cudaSuccess) return bfail(LBCG_ERR_CUDA, std::string("batch replay: ") + cudaGetErrorString(e));
+        for (int s = 0; s < b->max_slots; ++s) {
+            lbcg_ctx* c = b->ctx[s];
+            if (!c) continue;
+            const int n = b->h_slots[s].steps;
+            if (n & 1) std::swap(c->A, c->B);
+            c->step += n;
+            b->remaining[s] -= n;
+        }
+        done += chunk;
+    }
+    return LBCG_OK;
+}
+
+int lbcg_batch_poll(lbcg_batch* b, int* done_slots, int cap, int* ndone)
+{
+    if (!b || !ndone || (cap > 0 && !done_slots)) return bfail(LBCG_ERR_ARG, "null argument");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(LBCG_ERR_CUDA, cudaGetErrorString(e));
+    int n = 0;
+    for (int s = 0; s < b->max_slots && n < cap; ++s)
+        if (b->ctx[s] && b->remaining[s] == 0 && !b->reported[s]) {
+            done_slots[n++] = s;
+            b->reported[s] = 1;
+        }
+    *ndone = n;
+    return LBCG_OK;
+}
+
+}  // extern "C"

@@ -54,6 +54,26 @@ __host__ __device__ inline const Phys<float>& phys<float>(const KParams& P) { re
 template <>
 __host__ __device__ inline const Phys<double>& phys<double>(const KParams& P) { return P.pd; }
 
+// One instance of a batch as the batched kernels see it (device table, rewritten by the
+// host before each graph launch; the captured graph itself never changes).
+struct BatchSlot {
+    KParams kp;              // launch shape: D2Q9 rows 16, D3Q19 8 x 8 blocks, 8 planes
+    const void* a;           // current state (source of even steps of the launch)
+    void* b;                 // other buffer
+    const uint32_t* link;    // link words or nullptr
+    const int* ghost;        // port ghost table or nullptr
+    const double* ghost_u;
+    int nghost;
+    int steps;               // steps this launch advances the instance (0 = idle)
+};
+// work item: D2Q9 (slot, first strip, strip count <= 8, -); D3Q19 (slot, bx, by, bz);
+// port refill (slot, first ghost, ghost count <= 4, -)
+struct BatchItem {
+    int slot, x, y, z;
+};
+
+KParams make_kparams(const lbcg_params& p, const int dims[3], size_t np, int rows, int block_rows);
+
 constexpr int kMaxPartials = 1024;   // blocks of the deterministic reductions
 constexpr int kObsSlots = 16;
 constexpr int kGraphSteps = 32;   // steps per captured graph (even: A/B roles return)
@@ -86,6 +106,10 @@ struct lbcg_ctx {
     int* d_ghost = nullptr;            // [4][nghost]: site, inward neighbour, port, kind
     double* d_ghost_u = nullptr;       // [3][nghost] inlet velocity
     long long fluid_sites = 0;
+
+    // read-back / labelling / staging scratch (allocated on first use, kept)
+    void* d_scratch = nullptr;
+    size_t scratch_bytes = 0;
 
     // reductions
     double* d_partials = nullptr;      // kMaxPartials * kObsSlots
@@ -122,6 +146,11 @@ cudaError_t launch_pops_from_f64(lbcg_ctx* c, const double* f, void* a, int i);
 cudaError_t launch_observables(lbcg_ctx* c, const void* a, const double centre[3], double r_in, double r_out,
                                double* d_partials, double* d_result);
 cudaError_t launch_label(lbcg_ctx* c, const void* a, int32_t* parent, double* half, int* d_flag);
+// batched launchers (step.cu, aux.cu): one graph node each
+cudaError_t launch_batch_step(int lattice, int precision, const BatchSlot* slots, const BatchItem* items,
+                              const int* nitems, int k, cudaStream_t st);
+cudaError_t launch_batch_fill(int lattice, int precision, const BatchSlot* slots, const BatchItem* items,
+                              const int* nitems, int cap, int k, cudaStream_t st);
 
 void fill_kparams(lbcg_ctx* c);
 // noalloc.cu

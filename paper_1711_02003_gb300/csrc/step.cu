@@ -150,18 +150,16 @@ __device__ __forceinline__ void store_site(const KParams& P, typename Store<PREC
 }
 
 // ------------------------------------------------------------------------ D2Q9
+// one warp: the strip (sxi, syi) of 30 x rows sites
 template <int PREC, typename IDX>
-__global__ void __launch_bounds__(256) k_step_d2q9(const KParams P, const typename Store<PREC>::S* __restrict__ A,
-                                                   typename Store<PREC>::S* __restrict__ B,
-                                                   const uint32_t* __restrict__ link)
+__device__ __forceinline__ void strip_d2q9(const KParams& P, const typename Store<PREC>::S* __restrict__ A,
+                                           typename Store<PREC>::S* __restrict__ B, const uint32_t* __restrict__ link,
+                                           int sxi, int syi)
 {
     using T = typename Store<PREC>::T;
     using L = Lat<0>;
     constexpr int Q = 9;
     const int lane = threadIdx.x & 31;
-    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (gw >= P.nsx * P.nsy) return;  // warp-uniform
-    const int sxi = gw % P.nsx, syi = gw / P.nsx;
     const int nx = P.nx, ny = P.ny;
     const int x = sxi * 30 + lane - 1;
     int xs;
@@ -181,6 +179,7 @@ __global__ void __launch_bounds__(256) k_step_d2q9(const KParams P, const typena
 #pragma unroll
     for (int i = 0; i < Q; ++i) rb[i] = gb[i] = T(0);
 
+#pragma unroll 2
     for (int yy = y0 - 1; yy <= y1; ++yy) {
         int ys;
         const bool yok = wrap_coord(yy, ny, P.per[1], ys);
@@ -188,9 +187,7 @@ __global__ void __launch_bounds__(256) k_step_d2q9(const KParams P, const typena
         nbr_off(ys, ny, P.per[1], dym, dyp);
         u.ym = (long long)dym * nx;
         u.yp = (long long)dyp * nx;
-        T rn[Q], gn[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) rn[i] = gn[i] = T(0);
+        T rn[Q], gn[Q];  // set for fluid sites, the only ones collided
         T psi_n = psi_wall;
         bool fluid_n = false;
         const IDX s = (IDX)xs + (IDX)nx * (IDX)ys;
@@ -242,26 +239,35 @@ __global__ void __launch_bounds__(256) k_step_d2q9(const KParams P, const typena
     }
 }
 
+template <int PREC, typename IDX>
+__global__ void __launch_bounds__(256) k_step_d2q9(const KParams P, const typename Store<PREC>::S* __restrict__ A,
+                                                   typename Store<PREC>::S* __restrict__ B,
+                                                   const uint32_t* __restrict__ link)
+{
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (gw >= P.nsx * P.nsy) return;  // warp-uniform
+    strip_d2q9<PREC, IDX>(P, A, B, link, gw % P.nsx, gw / P.nsx);
+}
+
 // ----------------------------------------------------------------------- D3Q19
 // blockDim = (32, WY); warp w owns row y = by*(WY-2) + w - 1; rows 1..WY-2 collide.
+// one block: the tile (bx, by) of 30 x (WY-2) sites over the z-chunk bz; psi_s holds
+// 4 * WY * 32 values of shared memory
 template <int PREC, bool KEEP, typename IDX>
-__global__ void __launch_bounds__(256, 2) k_step_d3q19(const KParams P,
-                                                       const typename Store<PREC>::S* __restrict__ A,
-                                                       typename Store<PREC>::S* __restrict__ B,
-                                                       const uint32_t* __restrict__ link)
+__device__ __forceinline__ void tile_d3q19(const KParams& P, const typename Store<PREC>::S* __restrict__ A,
+                                           typename Store<PREC>::S* __restrict__ B, const uint32_t* __restrict__ link,
+                                           int bx, int by, int bz, typename Store<PREC>::T* psi_s)
 {
     using T = typename Store<PREC>::T;
     using L = Lat<1>;
     constexpr int Q = 19;
-    extern __shared__ unsigned char smem_raw[];
-    T* psi_s = reinterpret_cast<T*>(smem_raw);  // [4][WY][32]
     const int lane = threadIdx.x;
     const int w = threadIdx.y;
     const int WY = blockDim.y;
     const int nx = P.nx, ny = P.ny, nz = P.nz;
     const long long nxy = (long long)nx * ny;
-    const int x = blockIdx.x * 30 + lane - 1;
-    const int y = blockIdx.y * (WY - 2) + w - 1;
+    const int x = bx * 30 + lane - 1;
+    const int y = by * (WY - 2) + w - 1;
     int xs, ys;
     const bool xok = wrap_coord(x, nx, P.per[0], xs) && x <= nx;
     const bool yok = wrap_coord(y, ny, P.per[1], ys) && y <= ny;
@@ -275,7 +281,7 @@ __global__ void __launch_bounds__(256, 2) k_step_d3q19(const KParams P,
         u.yp = (long long)b * nx;
     }
     const IDX sxy = (IDX)xs + (IDX)nx * (IDX)ys;
-    const int z0 = blockIdx.z * P.rows;
+    const int z0 = bz * P.rows;
     const int z1 = min(z0 + P.rows, nz);
     const T psi_wall = phys<T>(P).psi_wall;
 
@@ -284,6 +290,7 @@ __global__ void __launch_bounds__(256, 2) k_step_d3q19(const KParams P,
 #pragma unroll
     for (int i = 0; i < Q; ++i) rb[i] = gb[i] = T(0);
 
+#pragma unroll 2
     for (int zz = z0 - 1; zz <= z1; ++zz) {
         int zs;
         const bool zok = wrap_coord(zz, nz, P.per[2], zs);
@@ -293,9 +300,7 @@ __global__ void __launch_bounds__(256, 2) k_step_d3q19(const KParams P,
             u.zm = (long long)a * nxy;
             u.zp = (long long)b * nxy;
         }
-        T rn[Q], gn[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) rn[i] = gn[i] = T(0);
+        T rn[Q], gn[Q];  // set for fluid sites, the only ones collided
         T psi_n = psi_wall;
         bool fluid_n = false;
         const IDX s = sxy + (IDX)nxy * (IDX)zs;
@@ -355,6 +360,333 @@ __global__ void __launch_bounds__(256, 2) k_step_d3q19(const KParams P,
     }
 }
 
+template <int PREC, bool KEEP, typename IDX>
+__global__ void __launch_bounds__(256, 2) k_step_d3q19(const KParams P,
+                                                       const typename Store<PREC>::S* __restrict__ A,
+                                                       typename Store<PREC>::S* __restrict__ B,
+                                                       const uint32_t* __restrict__ link)
+{
+    extern __shared__ unsigned char smem_raw[];
+    tile_d3q19<PREC, KEEP, IDX>(P, A, B, link, blockIdx.x, blockIdx.y, blockIdx.z,
+                                reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+}
+
+// ------------------------------------------------- pipelined variants (variant 3)
+// The collision of row/plane k needs psi of k+1, so a plain march waits for the loads of
+// k+1 and only then computes.  The pipelined march collides k-2 while the loads of k are
+// in flight: iteration k issues the pull of k, collides k-2 (its psi neighbours k-3..k-1
+// are known), then finishes psi(k).  D2Q9 keeps three rows of populations in registers;
+// D3Q19 parks the waiting plane's populations in a per-thread shared-memory stage.
+
+template <int PREC, typename IDX>
+__global__ void __launch_bounds__(256) k_step_d2q9_pipe(const KParams P,
+                                                        const typename Store<PREC>::S* __restrict__ A,
+                                                        typename Store<PREC>::S* __restrict__ B,
+                                                        const uint32_t* __restrict__ link)
+{
+    using T = typename Store<PREC>::T;
+    using L = Lat<0>;
+    constexpr int Q = 9;
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (gw >= P.nsx * P.nsy) return;  // warp-uniform
+    const int sxi = gw % P.nsx, syi = gw / P.nsx;
+    const int nx = P.nx, ny = P.ny;
+    const int x = sxi * 30 + lane - 1;
+    int xs;
+    const bool xok = wrap_coord(x, nx, P.per[0], xs) && x <= nx;
+    const bool xint = lane >= 1 && lane <= 30 && x < nx;
+    Up u;
+    nbr_off(xs, nx, P.per[0], u.xm, u.xp);
+    u.zm = u.zp = 0;
+    const int y0 = syi * P.rows;
+    const int y1 = min(y0 + P.rows, ny);
+    const T psi_wall = phys<T>(P).psi_wall;
+
+    T psi_a = psi_wall, psi_b = psi_wall, psi_c = psi_wall;  // rows k-3, k-2, k-1
+    T r1[Q], g1[Q], r2[Q], g2[Q];                           // populations of rows k-1, k-2
+    bool c1 = false, c2 = false;
+    IDX s1 = 0, s2 = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) r1[i] = g1[i] = r2[i] = g2[i] = T(0);
+
+    for (int yy = y0 - 1; yy <= y1 + 1; ++yy) {
+        T rn[Q], gn[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) rn[i] = gn[i] = T(0);
+        T psi_n = psi_wall;
+        bool fluid_n = false;
+        IDX s = 0;
+        if (yy <= y1) {
+            int ys;
+            const bool yok = wrap_coord(yy, ny, P.per[1], ys);
+            int dym, dyp;
+            nbr_off(ys, ny, P.per[1], dym, dyp);
+            u.ym = (long long)dym * nx;
+            u.yp = (long long)dyp * nx;
+            s = (IDX)xs + (IDX)nx * (IDX)ys;
+            if (xok && yok) {
+                const uint32_t lk = link ? __ldg(link + s) : 0u;
+                const uint32_t type = (lk >> kTypeShift) & 3u;
+                if (type == kTypeFluid) {
+                    psi_n = pull_fluid<0, PREC, IDX>(P, A, s, u, lk, rn, gn);
+                    fluid_n = true;
+                } else if (type == kTypePort) {
+                    psi_n = ghost_psi<0, PREC, IDX>(P, A, s);
+                }
+            }
+        }
+        if (yy - 2 >= y0) {  // warp-uniform: collide row yy-2 with psi rows a, b, c
+            const T am = __shfl_up_sync(0xffffffffu, psi_a, 1), ap = __shfl_down_sync(0xffffffffu, psi_a, 1);
+            const T bm = __shfl_up_sync(0xffffffffu, psi_b, 1), bp = __shfl_down_sync(0xffffffffu, psi_b, 1);
+            const T cm = __shfl_up_sync(0xffffffffu, psi_c, 1), cp = __shfl_down_sync(0xffffffffu, psi_c, 1);
+            if (c2) {
+                auto nb = [&](int cx, int cy) -> T {
+                    return cy < 0 ? (cx < 0 ? am : (cx > 0 ? ap : psi_a))
+                         : cy > 0 ? (cx < 0 ? cm : (cx > 0 ? cp : psi_c))
+                                  : (cx < 0 ? bm : (cx > 0 ? bp : psi_b));
+                };
+                T F[3] = {T(0), T(0), T(0)};
+#pragma unroll
+                for (int k = 0; k < L::NP; ++k) {
+                    const int p = L::rep(k);
+                    const int cx = L::cx(p), cy = L::cy(p);
+                    const T d = (T)L::w(p) * (nb(cx, cy) - nb(-cx, -cy));
+                    if (cx) F[0] += cx > 0 ? d : -d;
+                    if (cy) F[1] += cy > 0 ? d : -d;
+                }
+                F[0] *= T(3);
+                F[1] *= T(3);
+                collide_site<0, T>(P, phys<T>(P), r2, g2, F);
+                store_site<0, PREC, IDX>(P, B, s2, r2, g2);
+            }
+        }
+        psi_a = psi_b;
+        psi_b = psi_c;
+        psi_c = psi_n;
+        c2 = c1;
+        s2 = s1;
+        c1 = fluid_n && xint && yy >= y0 && yy < y1;
+        s1 = s;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            r2[i] = r1[i];
+            g2[i] = g1[i];
+            r1[i] = rn[i];
+            g1[i] = gn[i];
+        }
+    }
+}
+
+// blockDim = (32, WY); smem: psi [4][WY][32], population stages [2][2Q][WY*32]
+template <int PREC, typename IDX>
+__global__ void __launch_bounds__(256, 2) k_step_d3q19_pipe(const KParams P,
+                                                            const typename Store<PREC>::S* __restrict__ A,
+                                                            typename Store<PREC>::S* __restrict__ B,
+                                                            const uint32_t* __restrict__ link)
+{
+    using T = typename Store<PREC>::T;
+    using L = Lat<1>;
+    constexpr int Q = 19;
+    extern __shared__ unsigned char smem_raw[];
+    const int lane = threadIdx.x;
+    const int w = threadIdx.y;
+    const int WY = blockDim.y;
+    const int nthr = 32 * WY;
+    const int tid = w * 32 + lane;
+    T* psi_s = reinterpret_cast<T*>(smem_raw);  // [4][WY][32]
+    T* stage = psi_s + 4 * nthr;                 // [2][2Q][nthr]
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const long long nxy = (long long)nx * ny;
+    const int x = blockIdx.x * 30 + lane - 1;
+    const int y = blockIdx.y * (WY - 2) + w - 1;
+    int xs, ys;
+    const bool xok = wrap_coord(x, nx, P.per[0], xs) && x <= nx;
+    const bool yok = wrap_coord(y, ny, P.per[1], ys) && y <= ny;
+    const bool inner = lane >= 1 && lane <= 30 && x < nx && w >= 1 && w <= WY - 2 && y < ny;
+    Up u;
+    {
+        int a, b;
+        nbr_off(xs, nx, P.per[0], u.xm, u.xp);
+        nbr_off(ys, ny, P.per[1], a, b);
+        u.ym = (long long)a * nx;
+        u.yp = (long long)b * nx;
+    }
+    const IDX sxy = (IDX)xs + (IDX)nx * (IDX)ys;
+    const int z0 = blockIdx.z * P.rows;
+    const int z1 = min(z0 + P.rows, nz);
+    const T psi_wall = phys<T>(P).psi_wall;
+    bool c1 = false, c2 = false;  // planes k-1, k-2 collide here
+
+    for (int zz = z0 - 1; zz <= z1 + 1; ++zz) {
+        T rn[Q], gn[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) rn[i] = gn[i] = T(0);
+        T psi_n = psi_wall;
+        bool fluid_n = false;
+        if (zz <= z1) {
+            int zs;
+            const bool zok = wrap_coord(zz, nz, P.per[2], zs);
+            int a, b;
+            nbr_off(zs, nz, P.per[2], a, b);
+            u.zm = (long long)a * nxy;
+            u.zp = (long long)b * nxy;
+            const IDX s = sxy + (IDX)nxy * (IDX)zs;
+            if (xok && yok && zok) {
+                const uint32_t lk = link ? __ldg(link + s) : 0u;
+                const uint32_t type = (lk >> kTypeShift) & 3u;
+                if (type == kTypeFluid) {
+                    psi_n = pull_fluid<1, PREC, IDX>(P, A, s, u, lk, rn, gn);
+                    fluid_n = true;
+                } else if (type == kTypePort) {
+                    psi_n = ghost_psi<1, PREC, IDX>(P, A, s);
+                }
+            }
+        }
+        if (c2) {  // collide plane zc = zz-2 (psi of zc-1..zc+1 are in shared memory)
+            const int zc = zz - 2;
+            T* st = stage + (size_t)(zc & 1) * 2 * Q * nthr;
+            T rc[Q], gc[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                rc[i] = st[i * nthr + tid];
+                gc[i] = st[(Q + i) * nthr + tid];
+            }
+            auto nb = [&](int cx, int cy, int cz) -> T {
+                const int slot = (zc + cz - z0 + 1) & 3;
+                return psi_s[(slot * WY + (w + cy)) * 32 + (lane + cx)];
+            };
+            T F[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int k = 0; k < L::NP; ++k) {
+                const int p = L::rep(k);
+                const int cx = L::cx(p), cy = L::cy(p), cz = L::cz(p);
+                const T d = (T)L::w(p) * (nb(cx, cy, cz) - nb(-cx, -cy, -cz));
+                if (cx) F[0] += cx > 0 ? d : -d;
+                if (cy) F[1] += cy > 0 ? d : -d;
+                if (cz) F[2] += cz > 0 ? d : -d;
+            }
+            F[0] *= T(3);
+            F[1] *= T(3);
+            F[2] *= T(3);
+            collide_site<1, T>(P, phys<T>(P), rc, gc, F);
+            store_site<1, PREC, IDX>(P, B, sxy + (IDX)nxy * (IDX)zc, rc, gc);
+        }
+        c2 = c1;
+        c1 = fluid_n && inner && zz >= z0 && zz < z1;
+        if (c1) {  // park plane zz's populations (same slot as the plane just collided)
+            T* st = stage + (size_t)(zz & 1) * 2 * Q * nthr;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                st[i * nthr + tid] = rn[i];
+                st[(Q + i) * nthr + tid] = gn[i];
+            }
+        }
+        if (zz <= z1) psi_s[(((zz - z0 + 1) & 3) * WY + w) * 32 + lane] = psi_n;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------- batched kernels
+// Many instances advance in one launch: the blocks of a fixed (persistent) grid stride
+// over the work items of all instances, stage the item's instance parameters in shared
+// memory and run the same per-strip / per-tile code as the single-instance kernels, so
+// every instance's result is bit-identical to its solo run.  Node k of a captured graph
+// advances the instances with steps > k; even k reads buffer a, odd k reads buffer b.
+__device__ __forceinline__ void stage_params(KParams& dst, const KParams& src)
+{
+    const int nt = blockDim.x * blockDim.y;
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    const int* s = reinterpret_cast<const int*>(&src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int i = t; i < (int)(sizeof(KParams) / sizeof(int)); i += nt) d[i] = s[i];
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_batch_d2q9(const BatchSlot* __restrict__ slots,
+                                                    const BatchItem* __restrict__ items,
+                                                    const int* __restrict__ nitems, int k)
+{
+    using S = typename Store<PREC>::S;
+    __shared__ KParams sP;
+    const int n = *nitems;
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const BatchItem it = items[w];
+        const BatchSlot& sl = slots[it.slot];
+        if (k >= sl.steps) continue;  // block-uniform
+        __syncthreads();
+        stage_params(sP, sl.kp);
+        __syncthreads();
+        const bool odd = k & 1;
+        const S* src = (const S*)(odd ? sl.b : sl.a);
+        S* dst = (S*)(odd ? sl.a : sl.b);
+        const int wib = threadIdx.x >> 5;
+        if (wib < it.y) {
+            const int strip = it.x + wib;
+            strip_d2q9<PREC, int>(sP, src, dst, sl.link, strip % sP.nsx, strip / sP.nsx);
+        }
+    }
+}
+
+template <int PREC, bool KEEP>
+__global__ void __launch_bounds__(256, 2) k_batch_d3q19(const BatchSlot* __restrict__ slots,
+                                                        const BatchItem* __restrict__ items,
+                                                        const int* __restrict__ nitems, int k)
+{
+    using S = typename Store<PREC>::S;
+    using T = typename Store<PREC>::T;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ KParams sP;
+    const int n = *nitems;
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const BatchItem it = items[w];
+        const BatchSlot& sl = slots[it.slot];
+        if (k >= sl.steps) continue;  // block-uniform
+        __syncthreads();
+        stage_params(sP, sl.kp);
+        __syncthreads();
+        const bool odd = k & 1;
+        const S* src = (const S*)(odd ? sl.b : sl.a);
+        S* dst = (S*)(odd ? sl.a : sl.b);
+        tile_d3q19<PREC, KEEP, int>(sP, src, dst, sl.link, it.x, it.y, it.z, reinterpret_cast<T*>(smem_raw));
+    }
+}
+
+cudaError_t launch_batch_step(int lattice, int precision, const BatchSlot* slots, const BatchItem* items,
+                              const int* nitems, int k, cudaStream_t st)
+{
+    const int sms = 152;
+    if (lattice == LBCG_D2Q9) {
+        const unsigned grid = sms * 3;
+        switch (precision) {
+            case LBCG_FP64: k_batch_d2q9<LBCG_FP64><<<grid, 256, 0, st>>>(slots, items, nitems, k); break;
+            case LBCG_FP32: k_batch_d2q9<LBCG_FP32><<<grid, 256, 0, st>>>(slots, items, nitems, k); break;
+            case LBCG_FP32_DEV: k_batch_d2q9<LBCG_FP32_DEV><<<grid, 256, 0, st>>>(slots, items, nitems, k); break;
+            default: k_batch_d2q9<LBCG_FP16_SCALED><<<grid, 256, 0, st>>>(slots, items, nitems, k); break;
+        }
+    } else {
+        const unsigned grid = sms * 2;
+        const dim3 block(32, 8);
+        switch (precision) {
+            case LBCG_FP64:
+                k_batch_d3q19<LBCG_FP64, false><<<grid, block, 4 * 8 * 32 * sizeof(double), st>>>(slots, items, nitems, k);
+                break;
+            case LBCG_FP32:
+                k_batch_d3q19<LBCG_FP32, true><<<grid, block, 4 * 8 * 32 * sizeof(float), st>>>(slots, items, nitems, k);
+                break;
+            case LBCG_FP32_DEV:
+                k_batch_d3q19<LBCG_FP32_DEV, true><<<grid, block, 4 * 8 * 32 * sizeof(float), st>>>(slots, items,
+                                                                                                nitems, k);
+                break;
+            default:
+                k_batch_d3q19<LBCG_FP16_SCALED, true><<<grid, block, 4 * 8 * 32 * sizeof(float), st>>>(slots, items,
+                                                                                                   nitems, k);
+                break;
+        }
+    }
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------- launchers
 static bool small_index(const lbcg_ctx* c) { return (long long)2 * c->Q * (long long)c->np < (1LL << 31) - 1; }
 
@@ -367,6 +699,13 @@ static cudaError_t launch_d2q9(lbcg_ctx* c, const void* a, void* b)
     const int threads = 256;
     const long long blocks = (warps * 32 + threads - 1) / threads;
     const uint32_t* lk = c->any_link ? c->d_link : nullptr;
+    if (c->variant == 3) {
+        if (small_index(c))
+            k_step_d2q9_pipe<PREC, int><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk);
+        else
+            k_step_d2q9_pipe<PREC, long long><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk);
+        return cudaGetLastError();
+    }
     if (small_index(c))
         k_step_d2q9<PREC, int><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk);
     else
@@ -385,6 +724,18 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b)
     dim3 grid(P.nsx, P.nsy, P.nsz);
     size_t smem = 4 * (size_t)wy * 32 * sizeof(T);
     const uint32_t* lk = c->any_link ? c->d_link : nullptr;
+    if (c->variant == 3) {
+        const size_t smem3 = (4 + 2 * 2 * 19) * (size_t)wy * 32 * sizeof(T);
+        if (small_index(c)) {
+            cudaFuncSetAttribute(k_step_d3q19_pipe<PREC, int>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3);
+            k_step_d3q19_pipe<PREC, int><<<grid, block, smem3, c->stream>>>(P, (const S*)a, (S*)b, lk);
+        } else {
+            cudaFuncSetAttribute(k_step_d3q19_pipe<PREC, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem3);
+            k_step_d3q19_pipe<PREC, long long><<<grid, block, smem3, c->stream>>>(P, (const S*)a, (S*)b, lk);
+        }
+        return cudaGetLastError();
+    }
     if (small_index(c))
         k_step_d3q19<PREC, KEEP, int><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk);
     else

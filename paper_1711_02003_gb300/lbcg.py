@@ -82,6 +82,14 @@ _PROTOS = {
     "lbcg_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
     "lbcg_kernel_time": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong)]),
     "lbcg_set_launch": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
+    "lbcg_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp)]),
+    "lbcg_batch_destroy": (None, [_vp]),
+    "lbcg_batch_add": (C.c_int, [_vp, _vp, C.c_longlong, C.POINTER(C.c_int)]),
+    "lbcg_batch_remove": (C.c_int, [_vp, C.c_int]),
+    "lbcg_batch_remaining": (C.c_longlong, [_vp, C.c_int]),
+    "lbcg_batch_step": (C.c_int, [_vp, C.c_longlong]),
+    "lbcg_batch_poll": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(C.c_int)]),
+    "lbcg_batch_last_error": (C.c_char_p, []),
 }
 
 
@@ -248,6 +256,30 @@ class Simulation:
         k = min(nd.value, cap)
         return labels, counts[:k].copy(), vols[:k].copy(), nd.value
 
+    # ------------------------------------------------------------ checkpoints
+    def save(self, path: str):
+        """Write the stored state (FP64 populations of every site, as lbcg_get_populations
+        returns them) and the step count to an .npz file."""
+        np.savez(path, populations=self.populations(), step=self.step_count + getattr(self, "_step_offset", 0),
+                 lattice=self.pb.lattice, precision=self.precision, shape=np.array([self.pb.nx, self.pb.ny, self.pb.nz]))
+
+    @classmethod
+    def load(cls, path: str, pb, precision: int | None = None, stream=None, **launch) -> "Simulation":
+        """A Simulation of problem `pb` resumed from a checkpoint written by save()."""
+        d = np.load(path)
+        if int(d["lattice"]) != pb.lattice or list(d["shape"]) != [pb.nx, pb.ny, pb.nz]:
+            raise ValueError("checkpoint does not match the problem's lattice or box")
+        prec = int(d["precision"]) if precision is None else precision
+        sim = cls(pb, prec, stream=stream, init=False, **launch)
+        sim.set_populations(d["populations"])
+        sim._step_offset = int(d["step"])
+        return sim
+
+    @property
+    def total_steps(self) -> int:
+        """Steps since the initial state, across checkpoint/resume."""
+        return self.step_count + getattr(self, "_step_offset", 0)
+
     def set_kernel_timing(self, enable: bool):
         _check("lbcg_set_kernel_timing", _lib.lbcg_set_kernel_timing(self._h, int(bool(enable))))
 
@@ -265,3 +297,64 @@ def header_functions(header_path: str | None = None) -> list:
     text = open(hp).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(lbcg_[a-z0-9_]+)\s*\(", text)))
+
+
+class Batch:
+    """Many instances of one lattice and storage precision advanced together
+    (lbcg_batch_*).  Instances are Simulation objects; they must use the batch's stream."""
+
+    def __init__(self, lattice: int, precision: int = LBCG_FP32_DEV, max_instances: int = 64, stream=None):
+        import torch
+        L = load()
+        self.lattice, self.precision = lattice, precision
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = _vp()
+        st = L.lbcg_batch_create(int(lattice), int(precision), int(max_instances), _vp(self.stream.cuda_stream),
+                                 C.byref(h))
+        self._bcheck("lbcg_batch_create", st)
+        self._h = h
+        self.max_instances = max_instances
+        self.sims = {}
+
+    @staticmethod
+    def _bcheck(fn, st):
+        if st != LBCG_OK:
+            raise LbcgError(fn, st, _lib.lbcg_batch_last_error().decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lbcg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, sim: "Simulation", steps: int) -> int:
+        slot = C.c_int(-1)
+        self._bcheck("lbcg_batch_add", _lib.lbcg_batch_add(self._h, sim._h, int(steps), C.byref(slot)))
+        self.sims[slot.value] = sim
+        return slot.value
+
+    def remove(self, slot: int):
+        self._bcheck("lbcg_batch_remove", _lib.lbcg_batch_remove(self._h, int(slot)))
+        self.sims.pop(slot, None)
+
+    def remaining(self, slot: int) -> int:
+        return int(_lib.lbcg_batch_remaining(self._h, int(slot)))
+
+    def step(self, max_steps: int):
+        self._bcheck("lbcg_batch_step", _lib.lbcg_batch_step(self._h, int(max_steps)))
+
+    def poll(self) -> list:
+        cap = max(1, self.max_instances)
+        out = (C.c_int * cap)()
+        n = C.c_int(0)
+        self._bcheck("lbcg_batch_poll", _lib.lbcg_batch_poll(self._h, out, cap, C.byref(n)))
+        return [out[i] for i in range(n.value)]
+
+    @property
+    def active(self) -> int:
+        return len(self.sims)

@@ -320,3 +320,73 @@ def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
     u = _uniform(seed ^ 0x5DEECE66D, n)
     gaps = -np.log1p(-u) / rate
     return np.cumsum(gaps)
+
+
+def step_channel_2d(nx: int = 256, ny: int = 64, *, terrace_frac: float = 1 / 3, terrace_h: int | None = None,
+                    u_in: float = 0.002, tau_cont: float = 1.0, tau_disp: float = 1.0, A: float = 0.01,
+                    beta: float = 0.7) -> Problem:
+    """2D step emulsifier: a shallow terrace (height ny/4) opening into a full-height reservoir;
+    red velocity inlet over the terrace at x = 0, pressure outlet at x = nx-1."""
+    th = max(2, ny // 4) if terrace_h is None else terrace_h
+    tl = max(4, int(nx * terrace_frac))
+    m = np.full((ny, nx), WALL, dtype=np.uint8)
+    m[1:1 + th, 1:tl] = FLUID
+    m[1:ny - 1, tl:nx - 1] = FLUID
+    m[1:1 + th, 0] = PORT0 + 0
+    m[1:ny - 1, nx - 1] = PORT0 + 1
+    ports = [Port(VELOCITY_INLET, 0, +1, PARABOLIC, u_in, 1.0, 1.0), Port(PRESSURE_OUTLET, 0, -1, PARABOLIC, 0.0, 1.0, -1.0)]
+    psi = -np.ones((ny, nx))
+    psi[:, :tl // 2] = 1.0
+    mask = m.ravel()
+    rho_r, rho_b = _two_phase_fields(psi, 1.0, mask)
+    a = ALPHA_UNIT_RATIO[D2Q9]
+    return Problem(lattice=D2Q9, nx=nx, ny=ny, nz=1, periodic=(0, 0, 0), tau_r=tau_disp, tau_b=tau_cont, alpha_r=a,
+                   alpha_b=a, A=A, beta=beta, psi_wall=-1.0, mask=mask, ports=ports, rho_r=rho_r, rho_b=rho_b,
+                   u=None, name=f"2D step channel {nx}x{ny}")
+
+
+def cross_junction_3d(nx: int = 128, ny: int = 64, nz: int = 16, *, u_disp: float = 0.002, u_cont: float = 0.002,
+                      tau_cont: float = 1.0, tau_disp: float = 1.0, A: float = 0.01, beta: float = 0.7) -> Problem:
+    """The 2D cross junction extruded in z between walls at z = 0 and z = nz-1 (channel depth nz-2)."""
+    cw = max(4, ny // 3)
+    sl = max(2, (ny - cw) // 2)
+    nyy = 2 * sl + cw
+    base = cross_junction(nx=nx, channel_w=cw, side_x=max(2, nx // 4), side_len=sl, u_disp=u_disp, u_cont=u_cont,
+                          tau_cont=tau_cont, tau_disp=tau_disp, A=A, beta=beta, fill_x=max(2, nx // 5))
+    m2 = base.mask.reshape(nyy, nx)
+    m = np.full((nz, nyy, nx), WALL, dtype=np.uint8)
+    m[1:nz - 1] = m2[None]
+    psi2 = np.where(base.rho_r.reshape(nyy, nx) > 0.5, 1.0, -1.0)
+    psi = np.broadcast_to(psi2[None], (nz, nyy, nx))
+    mask = m.ravel()
+    rho_r, rho_b = _two_phase_fields(psi, 1.0, mask)
+    a = ALPHA_UNIT_RATIO[D3Q19]
+    return Problem(lattice=D3Q19, nx=nx, ny=nyy, nz=nz, periodic=(0, 0, 0), tau_r=tau_disp, tau_b=tau_cont,
+                   alpha_r=a, alpha_b=a, A=A, beta=beta, psi_wall=-1.0, mask=mask, ports=list(base.ports),
+                   rho_r=rho_r, rho_b=rho_b, u=None, name=f"3D cross junction {nx}x{nyy}x{nz}")
+
+
+def serving_problem(spec: dict, A: float = 0.01, tau_cont: float = 1.0) -> Problem:
+    """The Problem of one serving request (random_request).  Continuous phase tau = tau_cont;
+    dispersed viscosity = visc_ratio x continuous; inlet speed U from Ca = rho nu U / sigma with
+    sigma = 2 A tau_cont / 9 (the Laplace-law closed form), clipped to [1e-4, 0.02]."""
+    nu_c = (tau_cont - 0.5) / 3.0
+    tau_d = 0.5 + 3.0 * nu_c * spec["visc_ratio"]
+    sigma = 2.0 * A * tau_cont / 9.0
+    U = float(np.clip(spec["ca"] * sigma / nu_c, 1e-4, 0.02))
+    nx, ny, nz = spec["nx"], spec["ny"], spec["nz"]
+    if spec["lattice"] == D2Q9:
+        if spec["geom"] == "junction":
+            cw = max(4, ny // 3)
+            sl = max(2, (ny - cw) // 2)
+            pb = cross_junction(nx=nx, channel_w=cw, side_x=max(2, nx // 4), side_len=sl, u_disp=U, u_cont=U,
+                                tau_cont=tau_cont, tau_disp=tau_d, A=A, fill_x=max(2, nx // 5))
+        else:
+            pb = step_channel_2d(nx, ny, u_in=U, tau_cont=tau_cont, tau_disp=tau_d, A=A)
+    else:
+        if spec["geom"] == "junction":
+            pb = cross_junction_3d(nx, ny, nz, u_disp=U, u_cont=U, tau_cont=tau_cont, tau_disp=tau_d, A=A)
+        else:
+            pb = step_emulsifier(nx, ny, nz, terrace_len=max(4, nx // 3), terrace_h=max(2, nz // 4), u_in=U,
+                                 tau_cont=tau_cont, tau_disp=tau_d, A=A, fill_x=max(2, nx // 6), seed=spec["seed"])
+    return pb.replace(name=f"request {spec['seed']}: {pb.name}, Ca {spec['ca']:.2e}, ratio {spec['visc_ratio']:.2f}")

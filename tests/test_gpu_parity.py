@@ -115,21 +115,26 @@ def test_fp64_d3q19_step_emulsifier():
     assert np.abs(g.populations() - o.populations()).max() <= 1e-11
 
 
-@pytest.mark.parametrize("rows,block_rows", [(1, 3), (5, 7), (64, 8)])
-def test_launch_shape_does_not_change_results(rows, block_rows):
+# The same kernel under any launch shape gives bit-identical results; different kernel
+# variants (registers / re-read / pipelined) may contract multiply-adds differently, so they
+# are held to rounding level.
+@pytest.mark.parametrize("rows,block_rows,variant", [(1, 3, 0), (5, 7, 0), (64, 8, 0), (5, 7, 1), (64, 8, 2),
+                                                     (3, 5, 3), (8, 8, 3)])
+def test_launch_shape_does_not_change_results(rows, block_rows, variant):
     lb = _lb()
     pb = W.step_emulsifier(nx=50, ny=30, nz=10, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10)
-    a = lb.Simulation(pb, lb.LBCG_FP64)
-    b = lb.Simulation(pb, lb.LBCG_FP64, rows=rows, block_rows=block_rows)
-    a.step(30)
-    b.step(30)
-    assert np.array_equal(a.populations(), b.populations())
-    pb2 = W.static_droplet(W.D2Q9, 70, 12, ny=45)
-    a = lb.Simulation(pb2, lb.LBCG_FP32_DEV)
-    b = lb.Simulation(pb2, lb.LBCG_FP32_DEV, rows=rows)
-    a.step(30)
-    b.step(30)
-    assert np.array_equal(a.populations(), b.populations())
+    pb2 = W.cross_junction(nx=130, channel_w=16, side_x=40, side_len=12, fill_x=30)
+    for prob, br in ((pb, block_rows), (pb2, 0)):
+        for prec, tol in ((lb.LBCG_FP64, 1e-14), (lb.LBCG_FP32_DEV, 1e-6)):
+            a = lb.Simulation(prob, prec)
+            b = lb.Simulation(prob, prec, rows=rows, block_rows=br, variant=variant)
+            a.step(30)
+            b.step(30)
+            d = np.abs(a.populations() - b.populations()).max()
+            if variant == 0:
+                assert d == 0.0, (prob.name, prec, d)
+            else:
+                assert d <= tol, (prob.name, prec, d)
 
 
 def test_deterministic_repeat():
