@@ -228,6 +228,7 @@ def main():
     ap.add_argument("--precision", default="f32dev", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-autotune", action="store_true", help="library default launch shape")
     ap.add_argument("--serving-requests", type=int, default=64, help="0 disables the serving sample")
     ap.add_argument("--serving-steps-scale", type=float, default=0.25)
     ap.add_argument("--serving-baseline", type=int, default=6)
@@ -252,8 +253,16 @@ def main():
     fluid = pb.fluid_sites()
     stream = torch.cuda.current_stream()
 
+    # ---------------------------------------------------------------- launch shape (untimed)
+    shape = {}
+    tuned = None
+    if not args.no_autotune:
+        from paper_1711_02003_gb300 import autotune
+        tuned = autotune.autotune(pb, prec)
+        shape = {k: tuned[k] for k in ("rows", "block_rows", "variant")}
+
     # ---------------------------------------------------------------- device-resident run
-    sim = lbcg.Simulation(pb, prec, stream=stream)
+    sim = lbcg.Simulation(pb, prec, stream=stream, **shape)
     sim.step(args.warmup)
     sim.observables(centre, allow_diverged=True)
     torch.cuda.synchronize()
@@ -338,7 +347,10 @@ def main():
                    "precision": args.precision, "fluid_sites": fluid, "box_sites": n,
                    "steps_per_observable": OBS_EVERY, "l2": "state (2 buffers) larger than L2, no flush"
                    if 2 * sim.state_bytes > 4 * 129e6 else "state fits in L2 (not a roofline instance)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "launch": dict(shape, tuned=tuned is not None,
+                                  tuned_ms=None if tuned is None else tuned["ms"],
+                                  candidates=None if tuned is None else len(tuned["table"]))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "fused step", "bytes_per_site": bytes_per_site,
                      "kernel_ms_avg": k_avg_s * 1e3, "peak_source": peak_kind},

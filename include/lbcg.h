@@ -189,6 +189,12 @@ int lbcg_get_fields_device(lbcg_ctx* ctx, double* rho_r, double* rho_b, double* 
 int lbcg_get_populations(lbcg_ctx* ctx, double* host_f);
 int lbcg_set_populations(lbcg_ctx* ctx, const double* host_f);
 
+/* Raw stored state (the current population buffer, lbcg_state_bytes long, in the
+ * storage format) to / from host memory: lossless checkpoint and restore in every
+ * precision.  lbcg_set_state writes both buffers.  Synchronous. */
+int lbcg_get_state(lbcg_ctx* ctx, void* host, size_t bytes);
+int lbcg_set_state(lbcg_ctx* ctx, const void* host, size_t bytes);
+
 /* Observables (see lbcg_obs).  centre[3] in lattice units; r_in < 0 selects
  * r_eff/2 and r_out < 0 selects r_eff + 5 (the paper's interface width of about
  * 5 lattice units, Sec. III).  Synchronous.  Returns LBCG_ERR_DIVERGED (with *out

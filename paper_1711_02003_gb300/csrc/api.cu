@@ -167,6 +167,41 @@ void fill_kparams(lbcg_ctx* c)
 {
     if (c->p.lattice != LBCG_D2Q9 && c->block_rows <= 2) c->block_rows = 8;
     c->kp = make_kparams(c->p, c->dims, c->np, c->rows, c->block_rows);
+    c->kp.ntiles = c->d_tiles ? c->ntiles : 0;
+}
+
+// active-tile list of the current launch shape (walled geometries): tiles (2D strips of
+// 30 x rows, 3D blocks of 30 x (block_rows-2) x rows) holding at least one fluid site
+int build_tiles(lbcg_ctx* c)
+{
+    cudaFree(c->d_tiles);
+    c->d_tiles = nullptr;
+    c->ntiles = 0;
+    c->kp.ntiles = 0;
+    if (!c->geometry || !c->any_link) return LBCG_OK;
+    const KParams& k = c->kp;
+    const int nx = c->dims[0], ny = c->dims[1];
+    const long long ntot = (long long)k.nsx * k.nsy * k.nsz;
+    std::vector<char> on((size_t)ntot, 0);
+    const int ty = c->p.lattice == LBCG_D2Q9 ? k.rows : c->block_rows - 2;
+    const int tz = c->p.lattice == LBCG_D2Q9 ? 1 : k.rows;
+    for (long long s = 0; s < c->n; ++s) {
+        if (c->mask[s] != LBCG_MASK_FLUID) continue;
+        const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
+        on[(size_t)((x / 30) + (long long)k.nsx * ((y / ty) + (long long)k.nsy * (z / tz)))] = 1;
+    }
+    std::vector<int> list;
+    for (long long t = 0; t < ntot; ++t)
+        if (on[(size_t)t]) list.push_back((int)t);
+    if ((long long)list.size() == ntot) return LBCG_OK;  // nothing to skip
+    if (list.empty()) list.push_back(0);
+    if (cudaMalloc(&c->d_tiles, sizeof(int) * list.size()) != cudaSuccess)
+        return fail(LBCG_ERR_NOMEM, "tile list allocation failed");
+    if (cudaMemcpy(c->d_tiles, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(LBCG_ERR_CUDA, "tile list copy failed");
+    c->ntiles = (int)list.size();
+    c->kp.ntiles = c->ntiles;
+    return LBCG_OK;
 }
 
 }  // namespace lbcg
@@ -249,6 +284,7 @@ void lbcg_destroy(lbcg_ctx* c)
     drop_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     free_tables(c);
+    cudaFree(c->d_tiles);
     cudaFree(c->d_scratch);
     cudaFree(c->d_partials);
     cudaFree(c->d_result);
@@ -416,7 +452,7 @@ int lbcg_set_geometry(lbcg_ctx* c, const uint8_t* mask, const lbcg_port* ports, 
     c->fluid_sites = fluid;
     c->geometry = true;
     c->fields = false;
-    return LBCG_OK;
+    return build_tiles(c);
 }
 
 // device scratch of at least `bytes` for staging and read-back (never the state buffers,
@@ -694,6 +730,29 @@ int lbcg_set_populations(lbcg_ctx* c, const double* f)
     return LBCG_OK;
 }
 
+int lbcg_get_state(lbcg_ctx* c, void* host, size_t bytes)
+{
+    int st = need(c, true);
+    if (st) return st;
+    if (!host || bytes != c->state_bytes) return fail(LBCG_ERR_ARG, "host buffer must be lbcg_state_bytes long");
+    LBCG_CUDA(cudaMemcpyAsync(host, c->A, bytes, cudaMemcpyDeviceToHost, c->stream), "copy state");
+    LBCG_CUDA(cudaStreamSynchronize(c->stream), "state sync");
+    return LBCG_OK;
+}
+
+int lbcg_set_state(lbcg_ctx* c, const void* host, size_t bytes)
+{
+    int st = need(c, false);
+    if (st) return st;
+    if (!host || bytes != c->state_bytes) return fail(LBCG_ERR_ARG, "host buffer must be lbcg_state_bytes long");
+    LBCG_CUDA(cudaMemcpyAsync(c->A, host, bytes, cudaMemcpyHostToDevice, c->stream), "copy state");
+    st = mirror_state(c);
+    if (st) return st;
+    LBCG_CUDA(cudaStreamSynchronize(c->stream), "state sync");
+    c->fields = true;
+    return LBCG_OK;
+}
+
 int lbcg_observables(lbcg_ctx* c, const double centre[3], double r_in, double r_out, lbcg_obs* out)
 {
     int st = need(c, true);
@@ -812,14 +871,14 @@ int lbcg_set_launch(lbcg_ctx* c, int rows, int block_rows, int variant)
 {
     if (!c) return fail(LBCG_ERR_ARG, "null context");
     if (rows < 0 || block_rows < 0 || (block_rows > 0 && (block_rows < 3 || block_rows > 8)) || variant < 0 ||
-        variant > 3)
-        return fail(LBCG_ERR_ARG, "launch shape out of range (block_rows in 3..8, variant in 0..3)");
+        variant > 4)
+        return fail(LBCG_ERR_ARG, "launch shape out of range (block_rows in 3..8, variant in 0..4)");
     c->rows = rows;
     c->block_rows = block_rows;
     c->variant = variant;
     fill_kparams(c);
     drop_graphs(c);
-    return LBCG_OK;
+    return build_tiles(c);
 }
 
 }  // extern "C"

@@ -42,6 +42,7 @@ struct KParams {
     int lattice;
     int rows;               // marching length per warp / block
     int nsx, nsy, nsz;      // strips / blocks per axis
+    int ntiles;             // entries of the active-tile list (0: launch every tile)
     Phys<float> pf;
     Phys<double> pd;
     double alpha_r, alpha_b;
@@ -107,6 +108,10 @@ struct lbcg_ctx {
     double* d_ghost_u = nullptr;       // [3][nghost] inlet velocity
     long long fluid_sites = 0;
 
+    // tiles of the current launch shape that hold at least one fluid site (walled boxes only)
+    int* d_tiles = nullptr;
+    int ntiles = 0;
+
     // read-back / labelling / staging scratch (allocated on first use, kept)
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -153,6 +158,7 @@ cudaError_t launch_batch_fill(int lattice, int precision, const BatchSlot* slots
                               const int* nitems, int cap, int k, cudaStream_t st);
 
 void fill_kparams(lbcg_ctx* c);
+int build_tiles(lbcg_ctx* c);
 // noalloc.cu
 int noalloc_observables(const lbcg_params* p, const void* state, const uint8_t* mask, const double centre[3],
                         double r_in, double r_out, void* stream, lbcg_obs* out, std::string& err);

@@ -149,6 +149,37 @@ __device__ __forceinline__ void store_site(const KParams& P, typename Store<PREC
     }
 }
 
+// Tiles with at least one fluid site, when the geometry has walls: the launch covers only
+// those (P.ntiles entries of `tiles`, each the linear index of a 2D strip or a 3D block
+// tile); without a list every tile of the box is launched.
+__device__ __forceinline__ bool strip_of(const KParams& P, const int* __restrict__ tiles, int gw, int& sxi, int& syi)
+{
+    int t = gw;
+    if (tiles) {
+        if (gw >= P.ntiles) return false;
+        t = tiles[gw];
+    } else if (gw >= P.nsx * P.nsy) {
+        return false;
+    }
+    sxi = t % P.nsx;
+    syi = t / P.nsx;
+    return true;
+}
+
+__device__ __forceinline__ void block_of(const KParams& P, const int* __restrict__ tiles, int& bx, int& by, int& bz)
+{
+    if (tiles) {
+        const int t = tiles[blockIdx.x];
+        bx = t % P.nsx;
+        by = (t / P.nsx) % P.nsy;
+        bz = t / (P.nsx * P.nsy);
+    } else {
+        bx = blockIdx.x;
+        by = blockIdx.y;
+        bz = blockIdx.z;
+    }
+}
+
 // ------------------------------------------------------------------------ D2Q9
 // one warp: the strip (sxi, syi) of 30 x rows sites
 template <int PREC, typename IDX>
@@ -242,11 +273,12 @@ __device__ __forceinline__ void strip_d2q9(const KParams& P, const typename Stor
 template <int PREC, typename IDX>
 __global__ void __launch_bounds__(256) k_step_d2q9(const KParams P, const typename Store<PREC>::S* __restrict__ A,
                                                    typename Store<PREC>::S* __restrict__ B,
-                                                   const uint32_t* __restrict__ link)
+                                                   const uint32_t* __restrict__ link, const int* __restrict__ tiles)
 {
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (gw >= P.nsx * P.nsy) return;  // warp-uniform
-    strip_d2q9<PREC, IDX>(P, A, B, link, gw % P.nsx, gw / P.nsx);
+    int sxi, syi;
+    if (!strip_of(P, tiles, gw, sxi, syi)) return;  // warp-uniform
+    strip_d2q9<PREC, IDX>(P, A, B, link, sxi, syi);
 }
 
 // ----------------------------------------------------------------------- D3Q19
@@ -364,11 +396,12 @@ template <int PREC, bool KEEP, typename IDX>
 __global__ void __launch_bounds__(256, 2) k_step_d3q19(const KParams P,
                                                        const typename Store<PREC>::S* __restrict__ A,
                                                        typename Store<PREC>::S* __restrict__ B,
-                                                       const uint32_t* __restrict__ link)
+                                                       const uint32_t* __restrict__ link, const int* __restrict__ tiles)
 {
     extern __shared__ unsigned char smem_raw[];
-    tile_d3q19<PREC, KEEP, IDX>(P, A, B, link, blockIdx.x, blockIdx.y, blockIdx.z,
-                                reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+    int bx, by, bz;
+    block_of(P, tiles, bx, by, bz);
+    tile_d3q19<PREC, KEEP, IDX>(P, A, B, link, bx, by, bz, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
 }
 
 // ------------------------------------------------- pipelined variants (variant 3)
@@ -382,15 +415,16 @@ template <int PREC, typename IDX>
 __global__ void __launch_bounds__(256) k_step_d2q9_pipe(const KParams P,
                                                         const typename Store<PREC>::S* __restrict__ A,
                                                         typename Store<PREC>::S* __restrict__ B,
-                                                        const uint32_t* __restrict__ link)
+                                                        const uint32_t* __restrict__ link,
+                                                        const int* __restrict__ tiles)
 {
     using T = typename Store<PREC>::T;
     using L = Lat<0>;
     constexpr int Q = 9;
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (gw >= P.nsx * P.nsy) return;  // warp-uniform
-    const int sxi = gw % P.nsx, syi = gw / P.nsx;
+    int sxi, syi;
+    if (!strip_of(P, tiles, gw, sxi, syi)) return;  // warp-uniform
     const int nx = P.nx, ny = P.ny;
     const int x = sxi * 30 + lane - 1;
     int xs;
@@ -483,8 +517,11 @@ template <int PREC, typename IDX>
 __global__ void __launch_bounds__(256, 2) k_step_d3q19_pipe(const KParams P,
                                                             const typename Store<PREC>::S* __restrict__ A,
                                                             typename Store<PREC>::S* __restrict__ B,
-                                                            const uint32_t* __restrict__ link)
+                                                            const uint32_t* __restrict__ link,
+                                                            const int* __restrict__ tiles)
 {
+    int bx, by, bz;
+    block_of(P, tiles, bx, by, bz);
     using T = typename Store<PREC>::T;
     using L = Lat<1>;
     constexpr int Q = 19;
@@ -498,8 +535,8 @@ __global__ void __launch_bounds__(256, 2) k_step_d3q19_pipe(const KParams P,
     T* stage = psi_s + 4 * nthr;                 // [2][2Q][nthr]
     const int nx = P.nx, ny = P.ny, nz = P.nz;
     const long long nxy = (long long)nx * ny;
-    const int x = blockIdx.x * 30 + lane - 1;
-    const int y = blockIdx.y * (WY - 2) + w - 1;
+    const int x = bx * 30 + lane - 1;
+    const int y = by * (WY - 2) + w - 1;
     int xs, ys;
     const bool xok = wrap_coord(x, nx, P.per[0], xs) && x <= nx;
     const bool yok = wrap_coord(y, ny, P.per[1], ys) && y <= ny;
@@ -513,7 +550,7 @@ __global__ void __launch_bounds__(256, 2) k_step_d3q19_pipe(const KParams P,
         u.yp = (long long)b * nx;
     }
     const IDX sxy = (IDX)xs + (IDX)nx * (IDX)ys;
-    const int z0 = blockIdx.z * P.rows;
+    const int z0 = bz * P.rows;
     const int z1 = min(z0 + P.rows, nz);
     const T psi_wall = phys<T>(P).psi_wall;
     bool c1 = false, c2 = false;  // planes k-1, k-2 collide here
@@ -585,6 +622,187 @@ __global__ void __launch_bounds__(256, 2) k_step_d3q19_pipe(const KParams P,
         if (zz <= z1) psi_s[(((zz - z0 + 1) & 3) * WY + w) * 32 + lane] = psi_n;
         __syncthreads();
     }
+}
+
+// ----------------------------------------------- asynchronous-copy variant (variant 4)
+// D3Q19, 4-byte storage formats.  Each thread copies the pulled populations of its site
+// for plane zz+2 into its own shared-memory stage with cp.async while it computes psi of
+// plane zz and collides plane zz-1, so loads are in flight during the arithmetic instead of
+// between it.  Stages: zz-1 (collided), zz (psi), zz+1, zz+2 (in flight) -> 4 per thread.
+// The link word of a plane is read one iteration before its copies are issued.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kAsyncStages = 4;  // lookahead 2
+
+template <int PREC, typename IDX>
+__global__ void __launch_bounds__(256, 1) k_step_d3q19_async(const KParams P,
+                                                             const typename Store<PREC>::S* __restrict__ A,
+                                                             typename Store<PREC>::S* __restrict__ B,
+                                                             const uint32_t* __restrict__ link,
+                                                             const int* __restrict__ tiles)
+{
+    int bx, by, bz;
+    block_of(P, tiles, bx, by, bz);
+    using S = typename Store<PREC>::S;
+    using T = typename Store<PREC>::T;
+    using L = Lat<1>;
+    constexpr int Q = 19;
+    static_assert(sizeof(S) == 4, "4-byte storage only");
+    extern __shared__ unsigned char smem_raw[];
+    const int lane = threadIdx.x;
+    const int w = threadIdx.y;
+    const int WY = blockDim.y;
+    const int nthr = 32 * WY;
+    const int tid = w * 32 + lane;
+    T* psi_s = reinterpret_cast<T*>(smem_raw);        // [4][WY][32]
+    S* stage = reinterpret_cast<S*>(psi_s + 4 * nthr);  // [kAsyncStages][2Q][nthr]
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const long long nxy = (long long)nx * ny;
+    const int x = bx * 30 + lane - 1;
+    const int y = by * (WY - 2) + w - 1;
+    int xs, ys;
+    const bool xok = wrap_coord(x, nx, P.per[0], xs) && x <= nx;
+    const bool yok = wrap_coord(y, ny, P.per[1], ys) && y <= ny;
+    const bool inner = lane >= 1 && lane <= 30 && x < nx && w >= 1 && w <= WY - 2 && y < ny;
+    Up u;
+    {
+        int a, b;
+        nbr_off(xs, nx, P.per[0], u.xm, u.xp);
+        nbr_off(ys, ny, P.per[1], a, b);
+        u.ym = (long long)a * nx;
+        u.yp = (long long)b * nx;
+    }
+    const IDX sxy = (IDX)xs + (IDX)nx * (IDX)ys;
+    const IDX np = (IDX)P.np;
+    const int z0 = bz * P.rows;
+    const int z1 = min(z0 + P.rows, nz);
+    const Phys<T>& ph = phys<T>(P);
+    const T psi_wall = ph.psi_wall;
+    // site kind of a plane for this thread: 0 outside/wall, 1 fluid, 2 port ghost
+    auto kind_of = [&](int zz, uint32_t& lk, IDX& s, int& zs) -> int {
+        lk = 0;
+        s = 0;
+        zs = 0;
+        if (zz > z1) return 0;
+        const bool zok = wrap_coord(zz, nz, P.per[2], zs);
+        if (!(xok && yok && zok)) return 0;
+        s = sxy + (IDX)nxy * (IDX)zs;
+        lk = link ? __ldg(link + s) : 0u;
+        const uint32_t type = (lk >> kTypeShift) & 3u;
+        return type == kTypeFluid ? 1 : (type == kTypePort ? 2 : 0);
+    };
+    // issue the copies of plane zz (kind k) into its stage
+    auto issue = [&](int zz, int k, uint32_t lk, IDX s, int zs) {
+        S* st = stage + (size_t)((zz - z0 + 1) & (kAsyncStages - 1)) * 2 * Q * nthr;
+        if (k == 1) {
+            Up uu = u;
+            int a, b;
+            nbr_off(zs, nz, P.per[2], a, b);
+            uu.zm = (long long)a * nxy;
+            uu.zp = (long long)b * nxy;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const bool bounce = (lk >> i) & 1u;
+                const IDX ir = bounce ? (IDX)L::opp(i) * np + s : (IDX)i * np + s + up_off<1, IDX>(uu, i);
+                cp_async4(st + i * nthr + tid, A + ir);
+                cp_async4(st + (Q + i) * nthr + tid, A + ir + (IDX)Q * np);
+            }
+        } else if (k == 2) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const IDX ir = (IDX)i * np + s;
+                cp_async4(st + i * nthr + tid, A + ir);
+                cp_async4(st + (Q + i) * nthr + tid, A + ir + (IDX)Q * np);
+            }
+        }
+        cp_async_commit();
+    };
+    auto read_stage = [&](int zz, T (&r)[Q], T (&g)[Q]) {
+        const S* st = stage + (size_t)((zz - z0 + 1) & (kAsyncStages - 1)) * 2 * Q * nthr;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            // decode exactly as a global load would (Store::load on the staged element)
+            Store<PREC>::load(st, (IDX)(i * nthr + tid), (IDX)((Q + i) * nthr + tid), ph, L::cls(i), r[i], g[i]);
+        }
+    };
+
+    // prologue: planes z0-1 and z0 in flight, link of z0+1 known
+    int k_a, k_b, k_c, zs_a, zs_b, zs_c;
+    uint32_t lk_a, lk_b, lk_c;
+    IDX s_a, s_b, s_c;
+    k_a = kind_of(z0 - 1, lk_a, s_a, zs_a);
+    issue(z0 - 1, k_a, lk_a, s_a, zs_a);
+    k_b = kind_of(z0, lk_b, s_b, zs_b);
+    issue(z0, k_b, lk_b, s_b, zs_b);
+    k_c = kind_of(z0 + 1, lk_c, s_c, zs_c);
+    int kind_cur = k_a;       // kind of plane zz (for psi)
+    int kind_next = k_b;      // kind of plane zz+1
+    bool coll_b = false;      // plane zz-1 collides here
+    IDX sc_prev = 0;
+
+    for (int zz = z0 - 1; zz <= z1; ++zz) {
+        // 1. issue plane zz+2 (its link word was read last iteration), read the link of zz+3
+        issue(zz + 2, k_c, lk_c, s_c, zs_c);
+        const int kind_2 = k_c;
+        k_c = kind_of(zz + 3, lk_c, s_c, zs_c);
+        // 2. plane zz has landed (two newer groups may still be in flight)
+        cp_async_wait<2>();
+        T psi_n = psi_wall;
+        if (kind_cur != 0) {
+            T r[Q], g[Q];
+            read_stage(zz, r, g);
+            T rr = r[0], sg = g[0];
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                rr += r[i];
+                sg += g[i];
+            }
+            const T rho = ph.rho0 + sg;
+            psi_n = (rr - (rho - rr)) / rho;
+        }
+        psi_s[(((zz - z0 + 1) & 3) * WY + w) * 32 + lane] = psi_n;
+        __syncthreads();
+        // 3. collide plane zz-1
+        if (zz - 1 >= z0 && coll_b) {
+            const int zc = zz - 1;
+            T r[Q], g[Q];
+            read_stage(zc, r, g);
+            auto nb = [&](int cx, int cy, int cz) -> T {
+                const int slot = (zc + cz - z0 + 1) & 3;
+                return psi_s[(slot * WY + (w + cy)) * 32 + (lane + cx)];
+            };
+            T F[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int k = 0; k < L::NP; ++k) {
+                const int p = L::rep(k);
+                const int cx = L::cx(p), cy = L::cy(p), cz = L::cz(p);
+                const T d = (T)L::w(p) * (nb(cx, cy, cz) - nb(-cx, -cy, -cz));
+                if (cx) F[0] += cx > 0 ? d : -d;
+                if (cy) F[1] += cy > 0 ? d : -d;
+                if (cz) F[2] += cz > 0 ? d : -d;
+            }
+            F[0] *= T(3);
+            F[1] *= T(3);
+            F[2] *= T(3);
+            collide_site<1, T>(P, ph, r, g, F);
+            store_site<1, PREC, IDX>(P, B, sc_prev, r, g);
+        }
+        coll_b = kind_cur == 1 && inner && zz >= z0 && zz < z1;
+        sc_prev = sxy + (IDX)nxy * (IDX)(zz < 0 ? 0 : (zz >= nz ? 0 : zz));
+        kind_cur = kind_next;
+        kind_next = kind_2;
+    }
+    cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------- batched kernels
@@ -695,21 +913,22 @@ static cudaError_t launch_d2q9(lbcg_ctx* c, const void* a, void* b)
 {
     using S = typename Store<PREC>::S;
     const KParams& P = c->kp;
-    const long long warps = (long long)P.nsx * P.nsy;
+    const int* tl = c->d_tiles;
+    const long long warps = tl ? (long long)P.ntiles : (long long)P.nsx * P.nsy;
     const int threads = 256;
     const long long blocks = (warps * 32 + threads - 1) / threads;
     const uint32_t* lk = c->any_link ? c->d_link : nullptr;
     if (c->variant == 3) {
         if (small_index(c))
-            k_step_d2q9_pipe<PREC, int><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk);
+            k_step_d2q9_pipe<PREC, int><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
         else
-            k_step_d2q9_pipe<PREC, long long><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk);
+            k_step_d2q9_pipe<PREC, long long><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
         return cudaGetLastError();
     }
     if (small_index(c))
-        k_step_d2q9<PREC, int><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk);
+        k_step_d2q9<PREC, int><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
     else
-        k_step_d2q9<PREC, long long><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk);
+        k_step_d2q9<PREC, long long><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
     return cudaGetLastError();
 }
 
@@ -720,26 +939,42 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b)
     using T = typename Store<PREC>::T;
     const KParams& P = c->kp;
     const int wy = c->block_rows;
+    const int* tl = c->d_tiles;
     dim3 block(32, wy);
-    dim3 grid(P.nsx, P.nsy, P.nsz);
+    dim3 grid = tl ? dim3((unsigned)P.ntiles) : dim3(P.nsx, P.nsy, P.nsz);
     size_t smem = 4 * (size_t)wy * 32 * sizeof(T);
     const uint32_t* lk = c->any_link ? c->d_link : nullptr;
+    if constexpr (sizeof(S) == 4) {
+        if (c->variant == 4) {
+            const size_t smem4 = (4 * sizeof(T) + (size_t)kAsyncStages * 2 * 19 * sizeof(S)) * (size_t)wy * 32;
+            if (small_index(c)) {
+                cudaFuncSetAttribute(k_step_d3q19_async<PREC, int>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem4);
+                k_step_d3q19_async<PREC, int><<<grid, block, smem4, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+            } else {
+                cudaFuncSetAttribute(k_step_d3q19_async<PREC, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem4);
+                k_step_d3q19_async<PREC, long long><<<grid, block, smem4, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+            }
+            return cudaGetLastError();
+        }
+    }
     if (c->variant == 3) {
         const size_t smem3 = (4 + 2 * 2 * 19) * (size_t)wy * 32 * sizeof(T);
         if (small_index(c)) {
             cudaFuncSetAttribute(k_step_d3q19_pipe<PREC, int>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3);
-            k_step_d3q19_pipe<PREC, int><<<grid, block, smem3, c->stream>>>(P, (const S*)a, (S*)b, lk);
+            k_step_d3q19_pipe<PREC, int><<<grid, block, smem3, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
         } else {
             cudaFuncSetAttribute(k_step_d3q19_pipe<PREC, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem3);
-            k_step_d3q19_pipe<PREC, long long><<<grid, block, smem3, c->stream>>>(P, (const S*)a, (S*)b, lk);
+            k_step_d3q19_pipe<PREC, long long><<<grid, block, smem3, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
         }
         return cudaGetLastError();
     }
     if (small_index(c))
-        k_step_d3q19<PREC, KEEP, int><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk);
+        k_step_d3q19<PREC, KEEP, int><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
     else
-        k_step_d3q19<PREC, KEEP, long long><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk);
+        k_step_d3q19<PREC, KEEP, long long><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
     return cudaGetLastError();
 }
 

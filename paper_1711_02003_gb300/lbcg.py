@@ -75,6 +75,8 @@ _PROTOS = {
     "lbcg_get_fields_device": (C.c_int, [_vp, _vp, _vp, _vp]),
     "lbcg_get_populations": (C.c_int, [_vp, _vp]),
     "lbcg_set_populations": (C.c_int, [_vp, _vp]),
+    "lbcg_get_state": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "lbcg_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "lbcg_observables": (C.c_int, [_vp, _dp, C.c_double, C.c_double, C.POINTER(lbcg_obs)]),
     "lbcg_label": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.POINTER(C.c_int)]),
     "lbcg_observables_noalloc": (C.c_int, [C.POINTER(lbcg_params), _vp, _vp, _dp, C.c_double, C.c_double, _vp,
@@ -257,21 +259,29 @@ class Simulation:
         return labels, counts[:k].copy(), vols[:k].copy(), nd.value
 
     # ------------------------------------------------------------ checkpoints
+    def get_state(self) -> np.ndarray:
+        """The raw stored state (storage format bytes)."""
+        buf = np.empty(self.state_bytes, np.uint8)
+        _check("lbcg_get_state", _lib.lbcg_get_state(self._h, _ptr(buf), self.state_bytes))
+        return buf
+
+    def set_state(self, buf):
+        b = np.ascontiguousarray(buf, np.uint8)
+        _check("lbcg_set_state", _lib.lbcg_set_state(self._h, _ptr(b), b.size))
+
     def save(self, path: str):
-        """Write the stored state (FP64 populations of every site, as lbcg_get_populations
-        returns them) and the step count to an .npz file."""
-        np.savez(path, populations=self.populations(), step=self.step_count + getattr(self, "_step_offset", 0),
-                 lattice=self.pb.lattice, precision=self.precision, shape=np.array([self.pb.nx, self.pb.ny, self.pb.nz]))
+        """Checkpoint: the raw stored state (lossless in every precision) and the step count."""
+        np.savez(path, state=self.get_state(), step=self.total_steps, lattice=self.pb.lattice,
+                 precision=self.precision, shape=np.array([self.pb.nx, self.pb.ny, self.pb.nz]))
 
     @classmethod
-    def load(cls, path: str, pb, precision: int | None = None, stream=None, **launch) -> "Simulation":
+    def load(cls, path: str, pb, stream=None, **launch) -> "Simulation":
         """A Simulation of problem `pb` resumed from a checkpoint written by save()."""
         d = np.load(path)
         if int(d["lattice"]) != pb.lattice or list(d["shape"]) != [pb.nx, pb.ny, pb.nz]:
             raise ValueError("checkpoint does not match the problem's lattice or box")
-        prec = int(d["precision"]) if precision is None else precision
-        sim = cls(pb, prec, stream=stream, init=False, **launch)
-        sim.set_populations(d["populations"])
+        sim = cls(pb, int(d["precision"]), stream=stream, init=False, **launch)
+        sim.set_state(d["state"])
         sim._step_offset = int(d["step"])
         return sim
 

@@ -118,7 +118,7 @@ def test_fp64_d3q19_step_emulsifier():
 # The same kernel under any launch shape gives bit-identical results; different kernel
 # variants (registers / re-read / pipelined) may contract multiply-adds differently, so they
 # are held to rounding level.
-@pytest.mark.parametrize("rows,block_rows,variant", [(1, 3, 0), (5, 7, 0), (64, 8, 0), (5, 7, 1), (64, 8, 2),
+@pytest.mark.parametrize("rows,block_rows,variant", [(1, 3, 0), (5, 7, 0), (64, 8, 0), (5, 7, 1), (64, 8, 2), (3, 4, 4), (8, 8, 4),
                                                      (3, 5, 3), (8, 8, 3)])
 def test_launch_shape_does_not_change_results(rows, block_rows, variant):
     lb = _lb()
