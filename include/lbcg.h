@@ -195,6 +195,12 @@ int lbcg_set_populations(lbcg_ctx* ctx, const double* host_f);
 int lbcg_get_state(lbcg_ctx* ctx, void* host, size_t bytes);
 int lbcg_set_state(lbcg_ctx* ctx, const void* host, size_t bytes);
 
+/* Checkpoint file of the stored state: parameters, step count and raw state.  lbcg_load
+ * requires the same lattice, box and precision (LBCG_ERR_ARG otherwise), restores the
+ * step count and writes both buffers.  Synchronous. */
+int lbcg_save(lbcg_ctx* ctx, const char* path);
+int lbcg_load(lbcg_ctx* ctx, const char* path);
+
 /* Observables (see lbcg_obs).  centre[3] in lattice units; r_in < 0 selects
  * r_eff/2 and r_out < 0 selects r_eff + 5 (the paper's interface width of about
  * 5 lattice units, Sec. III).  Synchronous.  Returns LBCG_ERR_DIVERGED (with *out
@@ -280,8 +286,12 @@ int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
  * D3Q19: z planes per block); block_rows: D3Q19 warps per block along y (3..16);
  * variant: 0 default, 1 keep the next row/plane's populations in registers,
  * 2 re-read them when colliding, 3 pipelined (collide row/plane k-2 while the loads
- * of k are in flight).  Results are bit-identical across shapes and
- * variants; only speed changes.  Drops captured step graphs. */
+ * of k are in flight), 4 (D3Q19, 4-byte storage) asynchronous copies into a shared-
+ * memory ring, 5 (D3Q19) re-read compiled for three resident blocks per SM.  The
+ * default is the plain march for D2Q9 and, for D3Q19, variant 5 with 4- and 2-byte
+ * storage and variant 2 with FP64.  Within one variant results are bit-identical
+ * across shapes; variants may contract multiply-adds differently and agree to
+ * rounding.  Drops captured step graphs. */
 int lbcg_set_launch(lbcg_ctx* ctx, int rows, int block_rows, int variant);
 
 #ifdef __cplusplus

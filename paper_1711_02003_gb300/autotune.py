@@ -9,7 +9,8 @@ never changes results beyond rounding.
 Candidates:
   D2Q9 : rows per warp strip in {8, 16, 32, 64} x variant {0 plain march, 3 pipelined}
   D3Q19: warps per block along y in {4, 6, 8} x z-planes per block in {4, 8, 16} x
-         variant {1 registers, 2 re-read, 4 asynchronous copies (4-byte storage only)}
+         variant {5 re-read at three blocks per SM, 1 registers, 2 re-read,
+         4 asynchronous copies (4-byte storage only)}; FP64 tries {2, 1}
 """
 from __future__ import annotations
 
@@ -23,7 +24,7 @@ _CACHE = {}
 def candidates(lattice: int, precision: int) -> list:
     if lattice == lbcg.LBCG_D2Q9:
         return [dict(rows=r, block_rows=0, variant=v) for v, r in itertools.product((0, 3), (8, 16, 32, 64))]
-    variants = [1, 2] + ([4] if lbcg.ELEM_BYTES[precision] == 4 else [])
+    variants = [5, 1, 2] + ([4] if lbcg.ELEM_BYTES[precision] == 4 else [])
     if precision == lbcg.LBCG_FP64:
         variants = [2, 1]
     return [dict(rows=r, block_rows=b, variant=v) for v, b, r in itertools.product(variants, (4, 6, 8), (4, 8, 16))]

@@ -753,6 +753,61 @@ int lbcg_set_state(lbcg_ctx* c, const void* host, size_t bytes)
     return LBCG_OK;
 }
 
+// checkpoint file: "LBCGCKPT" | uint32 version 1 | lbcg_params | int64 step | uint64 bytes | state
+int lbcg_save(lbcg_ctx* c, const char* path)
+{
+    int st = need(c, true);
+    if (st) return st;
+    if (!path) return fail(LBCG_ERR_ARG, "null path");
+    std::vector<unsigned char> buf(c->state_bytes);
+    st = lbcg_get_state(c, buf.data(), buf.size());
+    if (st) return st;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(LBCG_ERR_ARG, std::string("cannot open ") + path);
+    const uint32_t ver = 1;
+    const long long step = c->step;
+    const uint64_t nb = c->state_bytes;
+    bool ok = std::fwrite("LBCGCKPT", 1, 8, f) == 8 && std::fwrite(&ver, sizeof(ver), 1, f) == 1 &&
+              std::fwrite(&c->p, sizeof(c->p), 1, f) == 1 && std::fwrite(&step, sizeof(step), 1, f) == 1 &&
+              std::fwrite(&nb, sizeof(nb), 1, f) == 1 && std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? LBCG_OK : fail(LBCG_ERR_ARG, std::string("write failed: ") + path);
+}
+
+int lbcg_load(lbcg_ctx* c, const char* path)
+{
+    int st = need(c, false);
+    if (st) return st;
+    if (!path) return fail(LBCG_ERR_ARG, "null path");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(LBCG_ERR_ARG, std::string("cannot open ") + path);
+    char magic[8];
+    uint32_t ver = 0;
+    lbcg_params p;
+    long long step = 0;
+    uint64_t nb = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "LBCGCKPT", 8) == 0 &&
+              std::fread(&ver, sizeof(ver), 1, f) == 1 && ver == 1 && std::fread(&p, sizeof(p), 1, f) == 1 &&
+              std::fread(&step, sizeof(step), 1, f) == 1 && std::fread(&nb, sizeof(nb), 1, f) == 1;
+    if (!ok) {
+        std::fclose(f);
+        return fail(LBCG_ERR_ARG, "not an lbcg checkpoint (version 1)");
+    }
+    if (p.lattice != c->p.lattice || p.nx != c->p.nx || p.ny != c->p.ny ||
+        (c->p.lattice == LBCG_D3Q19 && p.nz != c->p.nz) || p.precision != c->p.precision || nb != c->state_bytes) {
+        std::fclose(f);
+        return fail(LBCG_ERR_ARG, "checkpoint lattice, box or precision differs from the context");
+    }
+    std::vector<unsigned char> buf(nb);
+    ok = std::fread(buf.data(), 1, nb, f) == nb;
+    std::fclose(f);
+    if (!ok) return fail(LBCG_ERR_ARG, "truncated checkpoint");
+    st = lbcg_set_state(c, buf.data(), buf.size());
+    if (st) return st;
+    c->step = step;
+    return LBCG_OK;
+}
+
 int lbcg_observables(lbcg_ctx* c, const double centre[3], double r_in, double r_out, lbcg_obs* out)
 {
     int st = need(c, true);
@@ -871,8 +926,8 @@ int lbcg_set_launch(lbcg_ctx* c, int rows, int block_rows, int variant)
 {
     if (!c) return fail(LBCG_ERR_ARG, "null context");
     if (rows < 0 || block_rows < 0 || (block_rows > 0 && (block_rows < 3 || block_rows > 8)) || variant < 0 ||
-        variant > 4)
-        return fail(LBCG_ERR_ARG, "launch shape out of range (block_rows in 3..8, variant in 0..4)");
+        variant > 5)
+        return fail(LBCG_ERR_ARG, "launch shape out of range (block_rows in 3..8, variant in 0..5)");
     c->rows = rows;
     c->block_rows = block_rows;
     c->variant = variant;

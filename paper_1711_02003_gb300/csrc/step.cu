@@ -404,6 +404,19 @@ __global__ void __launch_bounds__(256, 2) k_step_d3q19(const KParams P,
     tile_d3q19<PREC, KEEP, IDX>(P, A, B, link, bx, by, bz, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
 }
 
+// variant 5: re-read variant compiled for three resident blocks per SM (<= 85 registers)
+template <int PREC, typename IDX>
+__global__ void __launch_bounds__(256, 3) k_step_d3q19_occ(const KParams P,
+                                                           const typename Store<PREC>::S* __restrict__ A,
+                                                           typename Store<PREC>::S* __restrict__ B,
+                                                           const uint32_t* __restrict__ link, const int* __restrict__ tiles)
+{
+    extern __shared__ unsigned char smem_raw[];
+    int bx, by, bz;
+    block_of(P, tiles, bx, by, bz);
+    tile_d3q19<PREC, false, IDX>(P, A, B, link, bx, by, bz, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+}
+
 // ------------------------------------------------- pipelined variants (variant 3)
 // The collision of row/plane k needs psi of k+1, so a plain march waits for the loads of
 // k+1 and only then computes.  The pipelined march collides k-2 while the loads of k are
@@ -933,7 +946,7 @@ static cudaError_t launch_d2q9(lbcg_ctx* c, const void* a, void* b)
 }
 
 template <int PREC, bool KEEP>
-static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b)
+static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant)
 {
     using S = typename Store<PREC>::S;
     using T = typename Store<PREC>::T;
@@ -945,7 +958,7 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b)
     size_t smem = 4 * (size_t)wy * 32 * sizeof(T);
     const uint32_t* lk = c->any_link ? c->d_link : nullptr;
     if constexpr (sizeof(S) == 4) {
-        if (c->variant == 4) {
+        if (variant == 4) {
             const size_t smem4 = (4 * sizeof(T) + (size_t)kAsyncStages * 2 * 19 * sizeof(S)) * (size_t)wy * 32;
             if (small_index(c)) {
                 cudaFuncSetAttribute(k_step_d3q19_async<PREC, int>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -959,7 +972,14 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b)
             return cudaGetLastError();
         }
     }
-    if (c->variant == 3) {
+    if (variant == 5 && !KEEP) {
+        if (small_index(c))
+            k_step_d3q19_occ<PREC, int><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+        else
+            k_step_d3q19_occ<PREC, long long><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+        return cudaGetLastError();
+    }
+    if (variant == 3) {
         const size_t smem3 = (4 + 2 * 2 * 19) * (size_t)wy * 32 * sizeof(T);
         if (small_index(c)) {
             cudaFuncSetAttribute(k_step_d3q19_pipe<PREC, int>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3);
@@ -989,19 +1009,21 @@ cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b)
             case LBCG_FP16_SCALED: return launch_d2q9<LBCG_FP16_SCALED>(c, a, b);
         }
     } else {
-        // default: FP64 re-reads the collided plane (register budget), others keep it
-        const bool keep = c->variant == 1 || (c->variant == 0 && prec != LBCG_FP64);
+        // default: 5 (re-read, three blocks per SM; measured fastest) for 4- and 2-byte storage;
+        // FP64 re-reads with two blocks per SM (it spills at the three-block register budget)
+        const int v = c->variant != 0 ? c->variant : (prec == LBCG_FP64 ? 2 : 5);
+        const bool keep = v == 1;
         switch (prec) {
             case LBCG_FP64:
-                return keep ? launch_d3q19<LBCG_FP64, true>(c, a, b) : launch_d3q19<LBCG_FP64, false>(c, a, b);
+                return keep ? launch_d3q19<LBCG_FP64, true>(c, a, b, v) : launch_d3q19<LBCG_FP64, false>(c, a, b, v);
             case LBCG_FP32:
-                return keep ? launch_d3q19<LBCG_FP32, true>(c, a, b) : launch_d3q19<LBCG_FP32, false>(c, a, b);
+                return keep ? launch_d3q19<LBCG_FP32, true>(c, a, b, v) : launch_d3q19<LBCG_FP32, false>(c, a, b, v);
             case LBCG_FP32_DEV:
-                return keep ? launch_d3q19<LBCG_FP32_DEV, true>(c, a, b)
-                            : launch_d3q19<LBCG_FP32_DEV, false>(c, a, b);
+                return keep ? launch_d3q19<LBCG_FP32_DEV, true>(c, a, b, v)
+                            : launch_d3q19<LBCG_FP32_DEV, false>(c, a, b, v);
             case LBCG_FP16_SCALED:
-                return keep ? launch_d3q19<LBCG_FP16_SCALED, true>(c, a, b)
-                            : launch_d3q19<LBCG_FP16_SCALED, false>(c, a, b);
+                return keep ? launch_d3q19<LBCG_FP16_SCALED, true>(c, a, b, v)
+                            : launch_d3q19<LBCG_FP16_SCALED, false>(c, a, b, v);
         }
     }
     return cudaErrorInvalidValue;

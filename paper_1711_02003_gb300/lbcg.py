@@ -77,6 +77,8 @@ _PROTOS = {
     "lbcg_set_populations": (C.c_int, [_vp, _vp]),
     "lbcg_get_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "lbcg_set_state": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "lbcg_save": (C.c_int, [_vp, C.c_char_p]),
+    "lbcg_load": (C.c_int, [_vp, C.c_char_p]),
     "lbcg_observables": (C.c_int, [_vp, _dp, C.c_double, C.c_double, C.POINTER(lbcg_obs)]),
     "lbcg_label": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.POINTER(C.c_int)]),
     "lbcg_observables_noalloc": (C.c_int, [C.POINTER(lbcg_params), _vp, _vp, _dp, C.c_double, C.c_double, _vp,
@@ -284,6 +286,14 @@ class Simulation:
         sim.set_state(d["state"])
         sim._step_offset = int(d["step"])
         return sim
+
+    def save_file(self, path: str):
+        """Checkpoint through the library's own file format (lbcg_save)."""
+        _check("lbcg_save", _lib.lbcg_save(self._h, path.encode()))
+
+    def load_file(self, path: str):
+        """Restore a lbcg_save checkpoint into this context (same lattice, box, precision)."""
+        _check("lbcg_load", _lib.lbcg_load(self._h, path.encode()))
 
     @property
     def total_steps(self) -> int:

@@ -38,3 +38,20 @@ def test_resume_is_exact(lb, tmp_path, precision, make):
     resumed.step(n)
     assert resumed.total_steps == 2 * n
     assert np.array_equal(resumed.populations(), whole.populations())
+
+
+def test_library_checkpoint_file(lb, tmp_path):
+    pb = W.cross_junction(nx=130, channel_w=16, side_x=40, side_len=12, fill_x=30)
+    a = lb.Simulation(pb, lb.LBCG_FP32_DEV)
+    a.step(21)
+    path = str(tmp_path / "ck.lbcg")
+    a.save_file(path)
+    b = lb.Simulation(pb, lb.LBCG_FP32_DEV, init=False)
+    b.load_file(path)
+    assert b.step_count == 21
+    a.step(21)
+    b.step(21)
+    assert np.array_equal(a.populations(), b.populations())
+    other = lb.Simulation(W.static_droplet(W.D2Q9, 32, 8), lb.LBCG_FP32_DEV)
+    with pytest.raises(lb.LbcgError):
+        other.load_file(path)
