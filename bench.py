@@ -9,8 +9,13 @@ deviation storage (the single large instance of the roofline measurement; its
 two state buffers, 2 x 478 MB, are larger than the 129 MB L2, so no L2 flush is
 needed between steps).  One bench step = one lattice update of the whole box.
 
+Timed region: K steps in chunks of 100 (three replays of the library's 32-step CUDA
+graph plus four individual launches) with the observables after each chunk.  The four
+individual step launches of every chunk are bracketed by CUDA events on the launching
+stream; their average duration is the kernel time of the roofline figure.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lbcg|reference]
-                       [--workload step_emulsifier|flow_focuser|droplet2d] [--precision f32dev|f32|f64|f16scaled]
+                       [--workload step_emulsifier|flow_focuser|droplet2d|droplet3d] [--precision f32dev|f32|f64|f16scaled]
 For N > 1 (torchrun), every rank runs an independent replica (the path has no
 exchange step on one box): value = all ranks' site updates / max-over-ranks time.
 """
@@ -39,16 +44,35 @@ OBS_EVERY = 100
 
 
 def make_workload(name: str):
-    if name == "step_emulsifier":
-        pb = W.step_emulsifier()
-        return pb, "3D step emulsifier D3Q19 768x128x32 (terrace 256x126x8, reservoir 512x126x30)", (384, 64, 16)
-    if name == "flow_focuser":
-        pb = W.cross_junction()
-        return pb, "2D flow-focusing cross junction D2Q9 1024x192 (main channel 64, side inlets 64 at x=256)", (512, 96)
-    if name == "droplet2d":
-        pb = W.static_droplet(W.D2Q9, 4096, 512)
-        return pb, "2D static droplet D2Q9 4096x4096 periodic, R=512", (2048, 2048)
-    raise SystemExit(f"unknown workload {name}")
+    try:
+        return W.named(name)
+    except ValueError as e:
+        raise SystemExit(str(e))
+
+
+def recorded_traffic(workload: str, precision: str, launch: dict):
+    """DRAM bytes (read + write) per launch of the step kernel, from an ncu record committed
+    under profiles/ for this workload, precision and launch shape, when the step-kernel
+    sources are unchanged since (their digest is part of the record); else None."""
+    from paper_1711_02003_gb300 import build as B
+    digest = B.step_kernel_digest()
+    want = {"workload": workload, "precision": precision, "variant": str(launch["variant"]),
+            "block_rows": str(launch["block_rows"]), "rows": str(launch["rows"]), "digest": digest}
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None, digest
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith((".md", ".txt")):
+            continue
+        with open(os.path.join(pdir, name)) as f:
+            for line in f:
+                line = line.strip().strip("`")
+                if not line.startswith("traffic-record:"):
+                    continue
+                kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+                if all(kv.get(k) == v for k, v in want.items()):
+                    return int(kv["dram_bytes"]), digest
+    return None, digest
 
 
 def peaks():
@@ -296,6 +320,8 @@ def main():
     k_avg_s = kms / klaunch * 1e-3
     achieved = bytes_per_site * fluid / k_avg_s / 1e9
     peak, peak_kind = peaks()
+    eff_launch = sim.launch
+    traffic, digest = recorded_traffic(args.workload, args.precision, eff_launch)
 
     # ---------------------------------------------------------------- end to end through host buffers
     n = pb.nsites
@@ -348,11 +374,14 @@ def main():
                    "steps_per_observable": OBS_EVERY, "l2": "state (2 buffers) larger than L2, no flush"
                    if 2 * sim.state_bytes > 4 * 129e6 else "state fits in L2 (not a roofline instance)",
                    "parallelism": f"replicas x{world}",
-                   "launch": dict(shape, tuned=tuned is not None,
+                   "launch": dict(eff_launch, tuned=tuned is not None,
                                   tuned_ms=None if tuned is None else tuned["ms"],
                                   candidates=None if tuned is None else len(tuned["table"]))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "fused step", "bytes_per_site": bytes_per_site,
+                     "traffic": traffic, "traffic_source": "ncu record in profiles/ (dram__bytes_read.sum + "
+                     "dram__bytes_write.sum, one launch)" if traffic else "no ncu record for this kernel source and "
+                     "launch shape", "algorithmic_bytes": bytes_per_site * fluid, "kernel_digest": digest,
+                     "kernel": "fused step", "bytes_per_site": bytes_per_site,
                      "kernel_ms_avg": k_avg_s * 1e3, "peak_source": peak_kind},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps, "h2d_bytes_total": h2d, "d2h_bytes_total": d2h,

@@ -275,24 +275,36 @@ int lbcg_batch_poll(lbcg_batch* batch, int* done_slots, int cap, int* ndone);
 /* Message of the calling thread's last failed batch call. */
 const char* lbcg_batch_last_error(void);
 
-/* Kernel timing: when enabled, CUDA events bracket every launch of the fused step
- * kernel on the context's stream; lbcg_kernel_time returns the summed duration in
- * milliseconds and the number of launches since the last reset (synchronises). */
+/* Kernel timing: when enabled, CUDA events bracket every fused step kernel that
+ * lbcg_step launches on its own, on the context's stream: the n mod 32 steps left after
+ * the 32-step CUDA graphs that lbcg_step replays (so every step when n < 32; graph
+ * replays stay untimed and unchanged).  lbcg_kernel_time returns the summed duration in
+ * milliseconds and the number of timed launches since the last reset (synchronises). */
 int lbcg_set_kernel_timing(lbcg_ctx* ctx, int enable);
 int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
 
 /* Launch shape of the fused step kernel (0 = library default):
  * rows: sites per warp along the marching axis (D2Q9: y rows per warp strip;
- * D3Q19: z planes per block); block_rows: D3Q19 warps per block along y (3..16);
+ * D3Q19: z planes per block); block_rows: D3Q19 warps per block along y (3..8; up to
+ * 16 with variant 7 and the regularized collision);
  * variant: 0 default, 1 keep the next row/plane's populations in registers,
  * 2 re-read them when colliding, 3 pipelined (collide row/plane k-2 while the loads
  * of k are in flight), 4 (D3Q19, 4-byte storage) asynchronous copies into a shared-
- * memory ring, 5 (D3Q19) re-read compiled for three resident blocks per SM.  The
- * default is the plain march for D2Q9 and, for D3Q19, variant 5 with 4- and 2-byte
- * storage and variant 2 with FP64.  Within one variant results are bit-identical
- * across shapes; variants may contract multiply-adds differently and agree to
+ * memory ring, 5 (D3Q19) re-read compiled for three resident blocks per SM,
+ * 6 (D3Q19, regularized) moment march: the waiting plane is held as the 11 moments the
+ * regularized collision needs (Eq. 11 rebuilds every population from them), so nothing
+ * is read twice, 7 the same with those moments in shared memory (64 registers).
+ * Variants 6 and 7 fall back to 5 (FP64: 2) for the BGK collision.  The default is the
+ * plain march for D2Q9; for D3Q19 with the regularized collision variant 7 (FP64: 6),
+ * with BGK variant 5 (FP64: 2).  Within one variant results are bit-identical across
+ * shapes; variants may contract multiply-adds and order sums differently and agree to
  * rounding.  Drops captured step graphs. */
 int lbcg_set_launch(lbcg_ctx* ctx, int rows, int block_rows, int variant);
+
+/* The launch shape the next step uses, after defaults: rows, block_rows (0 for D2Q9) and
+ * the kernel variant actually run (never 0; see lbcg_set_launch).  Null outputs are
+ * skipped. */
+int lbcg_get_launch(lbcg_ctx* ctx, int* rows, int* block_rows, int* variant);
 
 #ifdef __cplusplus
 }

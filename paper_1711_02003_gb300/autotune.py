@@ -9,25 +9,38 @@ never changes results beyond rounding.
 Candidates:
   D2Q9 : rows per warp strip in {8, 16, 32, 64} x variant {0 plain march, 3 pipelined}
   D3Q19: warps per block along y in {4, 6, 8} x z-planes per block in {4, 8, 16} x
-         variant {5 re-read at three blocks per SM, 1 registers, 2 re-read,
-         4 asynchronous copies (4-byte storage only)}; FP64 tries {2, 1}
+         variant; regularized collision {7, 6 moment march (shared-memory / register
+         moments), 5 re-read}, plus 12 and 16 warps per block for variant 7; BGK
+         {5, 1, 2, 4 (4-byte storage only)}; FP64 regularized {6, 2}, BGK {2, 1}
+
+Run as a program it prints the candidate table of one named workload, in launch order
+(each candidate: `warm` untimed then `steps` timed launches of its step kernel):
+
+    python -m paper_1711_02003_gb300.autotune --workload step_emulsifier --precision f32dev
 """
 from __future__ import annotations
 
+import argparse
 import itertools
+import json
 
 from . import lbcg
 
 _CACHE = {}
 
 
-def candidates(lattice: int, precision: int) -> list:
+def candidates(lattice: int, precision: int, collision: int = 0) -> list:
     if lattice == lbcg.LBCG_D2Q9:
         return [dict(rows=r, block_rows=0, variant=v) for v, r in itertools.product((0, 3), (8, 16, 32, 64))]
-    variants = [5, 1, 2] + ([4] if lbcg.ELEM_BYTES[precision] == 4 else [])
-    if precision == lbcg.LBCG_FP64:
-        variants = [2, 1]
-    return [dict(rows=r, block_rows=b, variant=v) for v, b, r in itertools.product(variants, (4, 6, 8), (4, 8, 16))]
+    f64 = precision == lbcg.LBCG_FP64
+    if collision == 0:  # regularized
+        variants = [6, 2] if f64 else [7, 6, 5]
+    else:
+        variants = [2, 1] if f64 else [5, 1, 2] + ([4] if lbcg.ELEM_BYTES[precision] == 4 else [])
+    out = [dict(rows=r, block_rows=b, variant=v) for v, b, r in itertools.product(variants, (4, 6, 8), (4, 8, 16))]
+    if 7 in variants:
+        out += [dict(rows=r, block_rows=b, variant=7) for b, r in itertools.product((12, 16), (4, 8))]
+    return out
 
 
 def kernel_ms(sim, steps: int = 30, warm: int = 5) -> float:
@@ -43,11 +56,11 @@ def kernel_ms(sim, steps: int = 30, warm: int = 5) -> float:
 
 def autotune(pb, precision: int, steps: int = 30, cands: list | None = None, cache: bool = True) -> dict:
     """Fastest launch shape for problem `pb`: {'rows', 'block_rows', 'variant', 'ms', 'table'}."""
-    key = (pb.lattice, pb.nx, pb.ny, pb.nz, precision, pb.fluid_sites())
+    key = (pb.lattice, pb.nx, pb.ny, pb.nz, precision, pb.collision, pb.fluid_sites())
     if cache and key in _CACHE:
         return _CACHE[key]
     table = []
-    for c in (cands or candidates(pb.lattice, precision)):
+    for c in (cands or candidates(pb.lattice, precision, pb.collision)):
         sim = lbcg.Simulation(pb, precision, **c)
         table.append(dict(c, ms=kernel_ms(sim, steps)))
         sim.close()
@@ -57,3 +70,32 @@ def autotune(pb, precision: int, steps: int = 30, cands: list | None = None, cac
     if cache:
         _CACHE[key] = out
     return out
+
+
+PRECISIONS = {"f64": 0, "f32": 1, "f32dev": 2, "f16scaled": 3}
+
+
+def main(argv=None):
+    from . import workloads as W
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--workload", default="step_emulsifier", choices=W.NAMED)
+    ap.add_argument("--precision", default="f32dev", choices=list(PRECISIONS))
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warm", type=int, default=5)
+    args = ap.parse_args(argv)
+    lbcg.load()
+    pb, desc, _ = W.named(args.workload)
+    prec = PRECISIONS[args.precision]
+    table = []
+    for c in candidates(pb.lattice, prec, pb.collision):
+        sim = lbcg.Simulation(pb, prec, **c)
+        table.append(dict(c, ms=kernel_ms(sim, args.steps, args.warm)))
+        sim.close()
+        del sim
+    best = min(table, key=lambda t: t["ms"])
+    print(json.dumps({"workload": desc, "precision": args.precision, "warm": args.warm, "steps": args.steps,
+                      "fluid_sites": pb.fluid_sites(), "best": best, "table": table}))
+
+
+if __name__ == "__main__":
+    main()

@@ -22,6 +22,20 @@ NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-rela
            "-Xptxas", "-warn-spills"]
 
 
+# sources that define the fused step kernels (a change invalidates recorded ncu counters)
+STEP_KERNEL_SOURCES = ["step.cu", "lbcg_device.cuh", "lbcg_internal.h"]
+
+
+def step_kernel_digest() -> str:
+    """First 16 hex digits of the SHA-256 of the step-kernel sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in STEP_KERNEL_SOURCES:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def nvcc() -> str:
     for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):

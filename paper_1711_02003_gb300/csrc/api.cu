@@ -152,7 +152,7 @@ KParams make_kparams(const lbcg_params& p, const int dims[3], size_t np, int row
         k.nsy = (k.ny + k.rows - 1) / k.rows;
         k.nsz = 1;
     } else {
-        // blocks of 32 x 8 threads (two resident per SM) marching 8 z-planes (measured best)
+        // blocks of 32 x 8 threads marching 8 z-planes (measured best)
         const int wy = block_rows > 2 ? block_rows : 8;
         k.nsx = (k.nx + 29) / 30;
         k.nsy = (k.ny + (wy - 2) - 1) / (wy - 2);
@@ -620,7 +620,7 @@ int lbcg_step(lbcg_ctx* c, long long nsteps)
     if (st) return st;
     if (nsteps < 0) return fail(LBCG_ERR_ARG, "negative step count");
     long long left = nsteps;
-    if (!c->timing && left >= kGraphSteps) {
+    if (left >= kGraphSteps) {
         while (left >= kGraphSteps) {
             cudaGraphExec_t exec = nullptr;
             st = graph_for_current(c, exec);
@@ -922,12 +922,25 @@ int lbcg_kernel_time(lbcg_ctx* c, double* total_ms, long long* launches)
     return LBCG_OK;
 }
 
+int lbcg_get_launch(lbcg_ctx* c, int* rows, int* block_rows, int* variant)
+{
+    if (!c) return fail(LBCG_ERR_ARG, "null context");
+    if (rows) *rows = c->kp.rows;
+    if (block_rows) *block_rows = c->p.lattice == LBCG_D2Q9 ? 0 : c->block_rows;
+    if (variant) *variant = effective_variant(c);
+    return LBCG_OK;
+}
+
 int lbcg_set_launch(lbcg_ctx* c, int rows, int block_rows, int variant)
 {
     if (!c) return fail(LBCG_ERR_ARG, "null context");
-    if (rows < 0 || block_rows < 0 || (block_rows > 0 && (block_rows < 3 || block_rows > 8)) || variant < 0 ||
-        variant > 5)
-        return fail(LBCG_ERR_ARG, "launch shape out of range (block_rows in 3..8, variant in 0..5)");
+    // the moment march with shared-memory moments (variant 7, regularized collision) takes
+    // blocks of up to 512 threads; every other kernel up to 256
+    const int max_wy = variant == 7 && c->p.collision == LBCG_REG ? 16 : 8;
+    if (rows < 0 || block_rows < 0 || (block_rows > 0 && (block_rows < 3 || block_rows > max_wy)) || variant < 0 ||
+        variant > 7)
+        return fail(LBCG_ERR_ARG,
+                    "launch shape out of range (block_rows in 3..8, 3..16 with variant 7; variant in 0..7)");
     c->rows = rows;
     c->block_rows = block_rows;
     c->variant = variant;

@@ -65,93 +65,107 @@ __device__ __forceinline__ void store_rb(const KParams& P, typename Store<PREC>:
 //   velocity:      f^k = f^{k,eq}(chi^k rho', u_port) + chi^k (f(x') - f^eq(x'))
 //   pressure:      f^k = f^{k,eq}(rho_port rho'^k / rho', u') + f^k(x') - f^{k,eq}(x')
 //   zero-gradient: f^k = f^k(x')
-// One warp per ghost: lane i < Q handles direction i; the moments of x' are warp sums.
-// Arithmetic in FP64 whatever the storage (only the few thousand port sites; f - f^eq of
-// plain populations would lose the deviation format's precision in FP32).
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
+// One thread per ghost, in the storage format's compute type, on the register form
+// (r_i = f^R_i, g_i = f_i - w_i rho0): every quantity formed is a small deviation, so
+// FP32 keeps the precision of the stored populations.  With phi^k_i = w_i + dphi^k_i and
+// P_i(u) = 3 c.u + 4.5 (c.u)^2 - 1.5 u^2:
+//   f^eq_i - w_i rho0 = w_i (rho - rho0) + rho_R dphi^R_i + rho_B dphi^B_i + w_i rho P_i(u),
+//   f^{R,eq}_i(rho_R, u) = rho_R (phi^R_i + w_i P_i(u)),
+// and the pressure rule reduces to f^k_i(x') + (rho_port / rho' - 1) f^{k,eq}_i(x').
 template <int LAT, int PREC>
 __device__ __forceinline__ void fill_one(const KParams& P, typename Store<PREC>::S* __restrict__ a,
                                          const int* __restrict__ tab, const double* __restrict__ gu, int ng, int t)
 {
     using L = Lat<LAT>;
     using SP = Store<PREC>;
-    using T = double;
+    using T = typename SP::T;
     constexpr int Q = L::Q;
-    const int lane = threadIdx.x & 31;
-    const Phys<double>& ph = P.pd;
+    const Phys<T>& ph = phys<T>(P);
+    const size_t np = P.np;
     const size_t g = (size_t)tab[t];
     const size_t xp = (size_t)tab[ng + t];
     const int kind = tab[3 * ng + t];
-    const bool act = lane < Q;
-    const int i = act ? lane : 0;
+    T r[Q], d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) SP::load(a, i * np + xp, (Q + i) * np + xp, ph, L::cls(i), r[i], d[i]);
     if (kind == LBCG_PORT_ZERO_GRADIENT) {
-        if (act) {
-            typename SP::T r, gg;
-            const Phys<typename SP::T>& pt = phys<typename SP::T>(P);
-            SP::load(a, (size_t)i * P.np + xp, (size_t)(Q + i) * P.np + xp, pt, L::cls(i), r, gg);
-            SP::store(a, (size_t)i * P.np + g, (size_t)(Q + i) * P.np + g, pt, L::cls(i), r, gg);
-        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) SP::store(a, i * np + g, (Q + i) * np + g, ph, L::cls(i), r[i], d[i]);
         return;
     }
-    T fr = 0, fb = 0;
-    if (act) load_rb<LAT, PREC>(P, a, i, xp, fr, fb);
-    const T f = fr + fb;
-    const T rr = warp_sum(fr), rb = warp_sum(fb);
-    const T jx = warp_sum(f * (T)L::cx(i)), jy = warp_sum(f * (T)L::cy(i)), jz = warp_sum(f * (T)L::cz(i));
-    if (!act) return;
-    const T rho = rr + rb;
-    const T ux = jx / rho, uy = jy / rho, uz = jz / rho;
-    T gr, gb;
-    if (kind == LBCG_PORT_VELOCITY) {
-        const T vx = gu[t], vy = gu[ng + t], vz = gu[2 * ng + t];
-        const T psi = gu[4 * ng + t];
-        const T xr = (1.0 + psi) / 2.0, xb = (1.0 - psi) / 2.0;
-        const T fneq = f - (feq_comp<LAT, T>(ph.phiR, rr, ux, uy, uz, i) + feq_comp<LAT, T>(ph.phiB, rb, ux, uy, uz, i));
-        gr = feq_comp<LAT, T>(ph.phiR, xr * rho, vx, vy, vz, i) + xr * fneq;
-        gb = feq_comp<LAT, T>(ph.phiB, xb * rho, vx, vy, vz, i) + xb * fneq;
-    } else {
-        const T rho_out = gu[3 * ng + t];
-        gr = feq_comp<LAT, T>(ph.phiR, rho_out * rr / rho, ux, uy, uz, i) +
-             (fr - feq_comp<LAT, T>(ph.phiR, rr, ux, uy, uz, i));
-        gb = feq_comp<LAT, T>(ph.phiB, rho_out * rb / rho, ux, uy, uz, i) +
-             (fb - feq_comp<LAT, T>(ph.phiB, rb, ux, uy, uz, i));
+    T rr = 0, dr = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        rr += r[i];
+        dr += d[i];
+        if (L::cx(i)) jx += L::cx(i) > 0 ? d[i] : -d[i];
+        if (L::cy(i)) jy += L::cy(i) > 0 ? d[i] : -d[i];
+        if (L::cz(i)) jz += L::cz(i) > 0 ? d[i] : -d[i];
     }
-    store_rb<LAT, PREC>(P, a, i, g, gr, gb);
+    const T rho = ph.rho0 + dr;
+    const T rb = rho - rr;
+    const T inv_rho = T(1) / rho;
+    const T ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+    const T usq = ux * ux + uy * uy + uz * uz;
+    if (kind == LBCG_PORT_VELOCITY) {
+        const T vx = (T)gu[t], vy = (T)gu[ng + t], vz = (T)gu[2 * ng + t];
+        const T psi = (T)gu[4 * ng + t];
+        const T xr = (T(1) + psi) * T(0.5), xb = (T(1) - psi) * T(0.5);
+        const T vsq = vx * vx + vy * vy + vz * vz;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int c = L::cls(i);
+            const T wi = (T)L::w(i);
+            const T cu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
+            const T cv = (T)L::cx(i) * vx + (T)L::cy(i) * vy + (T)L::cz(i) * vz;
+            const T pu = T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq;
+            const T pv = T(3) * cv + T(4.5) * cv * cv - T(1.5) * vsq;
+            const T neq = d[i] - (wi * dr + rr * ph.dphiR[c] + rb * ph.dphiB[c] + wi * rho * pu);
+            const T gr = xr * rho * (ph.phiR[c] + wi * pv) + xr * neq;
+            const T gd = wi * dr + xr * rho * ph.dphiR[c] + xb * rho * ph.dphiB[c] + wi * rho * pv + neq;
+            SP::store(a, i * np + g, (Q + i) * np + g, ph, c, gr, gd);
+        }
+    } else {
+        const T fac = (T)gu[3 * ng + t] * inv_rho - T(1);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int c = L::cls(i);
+            const T wi = (T)L::w(i);
+            const T cu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
+            const T pu = wi * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq);
+            const T er = rr * (ph.phiR[c] + pu), eb = rb * (ph.phiB[c] + pu);
+            SP::store(a, i * np + g, (Q + i) * np + g, ph, c, r[i] + fac * er, d[i] + fac * (er + eb));
+        }
+    }
 }
 
+constexpr int kFillThreads = 64;
+
 template <int LAT, int PREC>
-__global__ void __launch_bounds__(128) k_fill_ports(const KParams P, typename Store<PREC>::S* __restrict__ a,
-                                                    const int* __restrict__ tab, const double* __restrict__ gu,
-                                                    int ng)
+__global__ void __launch_bounds__(kFillThreads) k_fill_ports(const KParams P, typename Store<PREC>::S* __restrict__ a,
+                                                             const int* __restrict__ tab,
+                                                             const double* __restrict__ gu, int ng)
 {
-    const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (t >= ng) return;  // warp-uniform
+    const int t = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (t >= ng) return;
     fill_one<LAT, PREC>(P, a, tab, gu, ng, t);
 }
 
-// batched refill: work item (slot, first ghost, count <= 4); warp w of the block takes one
+// batched refill: work item (slot, first ghost, count <= kFillThreads), one thread per
 // ghost; node k refills the source buffer of step k of instances with steps > k
 template <int LAT, int PREC>
-__global__ void __launch_bounds__(128) k_batch_fill(const BatchSlot* __restrict__ slots,
-                                                    const BatchItem* __restrict__ items,
-                                                    const int* __restrict__ nitems, int k)
+__global__ void __launch_bounds__(kFillThreads) k_batch_fill(const BatchSlot* __restrict__ slots,
+                                                             const BatchItem* __restrict__ items,
+                                                             const int* __restrict__ nitems, int k)
 {
     const int w = blockIdx.x;
     if (w >= *nitems) return;
     const BatchItem it = items[w];
     const BatchSlot& sl = slots[it.slot];
     if (k >= sl.steps) return;
-    const int wib = threadIdx.x >> 5;
-    if (wib >= it.y) return;
+    if ((int)threadIdx.x >= it.y) return;
     typename Store<PREC>::S* src = (typename Store<PREC>::S*)((k & 1) ? sl.b : sl.a);
-    fill_one<LAT, PREC>(sl.kp, src, sl.ghost, sl.ghost_u, sl.nghost, it.x + wib);
+    fill_one<LAT, PREC>(sl.kp, src, sl.ghost, sl.ghost_u, sl.nghost, it.x + (int)threadIdx.x);
 }
 
 // ---------------------------------------------------------------- initial state
@@ -349,9 +363,10 @@ using SOf = typename Store<PREC>::S;
 cudaError_t launch_fill_ports(lbcg_ctx* c, void* a)
 {
     if (c->nghost == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((c->nghost + 3) / 4);  // 4 warps (ghosts) per block
-#define F_(LAT, PREC) \
-    k_fill_ports<LAT, PREC><<<blocks, 128, 0, c->stream>>>(c->kp, (SOf<PREC>*)a, c->d_ghost, c->d_ghost_u, c->nghost)
+    const unsigned blocks = (unsigned)((c->nghost + kFillThreads - 1) / kFillThreads);  // a thread per ghost
+#define F_(LAT, PREC)                                                                                   \
+    k_fill_ports<LAT, PREC><<<blocks, kFillThreads, 0, c->stream>>>(c->kp, (SOf<PREC>*)a, c->d_ghost, \
+                                                                    c->d_ghost_u, c->nghost)
     LBCG_DISPATCH(c, F_);
 #undef F_
     return cudaGetLastError();
@@ -361,7 +376,7 @@ cudaError_t launch_batch_fill(int lattice, int precision, const BatchSlot* slots
                               const int* nitems, int cap, int k, cudaStream_t st)
 {
     if (cap <= 0) return cudaSuccess;
-#define BF_(LAT, PREC) k_batch_fill<LAT, PREC><<<(unsigned)cap, 128, 0, st>>>(slots, items, nitems, k)
+#define BF_(LAT, PREC) k_batch_fill<LAT, PREC><<<(unsigned)cap, kFillThreads, 0, st>>>(slots, items, nitems, k)
     if (lattice == LBCG_D2Q9) {
         if (precision == LBCG_FP64) BF_(0, LBCG_FP64);
         else if (precision == LBCG_FP32) BF_(0, LBCG_FP32);

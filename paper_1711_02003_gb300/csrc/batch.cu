@@ -75,7 +75,7 @@ int rebuild(lbcg_batch* b)
                     for (int x = 0; x < k.nsx; ++x) b->h_items.push_back({s, x, y, z});
         }
         const int ng = b->ctx[s]->nghost;
-        for (int f = 0; f < ng; f += 4) b->h_fill.push_back({s, f, std::min(4, ng - f), 0});
+        for (int f = 0; f < ng; f += 64) b->h_fill.push_back({s, f, std::min(64, ng - f), 0});  // a thread per ghost
     }
     const int ni = (int)b->h_items.size(), nf = (int)b->h_fill.size();
     if (ni > b->items_cap || nf > b->fill_cap) {

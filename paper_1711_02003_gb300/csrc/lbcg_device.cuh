@@ -309,4 +309,139 @@ __device__ __forceinline__ void collide_site(const KParams& P, const Phys<T>& ph
     r[0] = rhoR - rsum;
 }
 
+
+// ------------------------------------------------------- the collision from moments
+// The regularized collision (Eq. 11) rebuilds every post-collision population from the
+// site's moments: rho_R, rho, the momentum, the second moment Pi of the streamed
+// populations, and the colour gradient F.  None of the individual streamed
+// populations is needed once these are summed, so a kernel can accumulate them while
+// the pulled populations arrive and keep 11 numbers per waiting site instead of 2Q.
+// The arithmetic is that of collide_site's regularized branch; only the order of the
+// sums differs (Pi^neq = Pi - Pi^eq instead of sum_i (f_i - feq_i) c_i c_i).
+template <typename T>
+struct SiteMom {
+    T rr, sg;                        // rho_R; rho - rho0 (sum of the total deviations g_i)
+    T jx, jy, jz;                    // momentum (sum_i g_i c_i)
+    T pxx, pyy, pzz, pxy, pxz, pyz;  // sum_i g_i c_ia c_ib
+};
+
+template <typename T>
+__device__ __forceinline__ void mom_zero(SiteMom<T>& m)
+{
+    m.rr = m.sg = m.jx = m.jy = m.jz = T(0);
+    m.pxx = m.pyy = m.pzz = m.pxy = m.pxz = m.pyz = T(0);
+}
+
+// add the opposite pair (p = rep(k), opp(p)); FULL = false sums only rho_R and rho
+template <int LAT, bool FULL, typename T>
+__device__ __forceinline__ void mom_add_pair(SiteMom<T>& m, int k, T rp, T gp, T rq, T gq)
+{
+    using L = Lat<LAT>;
+    const int p = L::rep(k);
+    m.rr += rp + rq;
+    const T ge = gp + gq;
+    m.sg += ge;
+    if (!FULL) return;
+    const T go = gp - gq;
+    const int ax = L::cx(p), ay = L::cy(p), az = L::cz(p);
+    if (ax) m.jx += ax > 0 ? go : -go;
+    if (ay) m.jy += ay > 0 ? go : -go;
+    if (az) m.jz += az > 0 ? go : -go;
+    if (ax) m.pxx += ge;
+    if (ay) m.pyy += ge;
+    if (az) m.pzz += ge;
+    if (ax && ay) m.pxy += (ax * ay > 0) ? ge : -ge;
+    if (ax && az) m.pxz += (ax * az > 0) ? ge : -ge;
+    if (ay && az) m.pyz += (ay * az > 0) ? ge : -ge;
+}
+
+// Regularized collision, perturbation and recolouring of one site from its moments;
+// out(i, r_i, g_i) receives every post-collision population (the rest direction last).
+template <int LAT, typename T, typename Out>
+__device__ __forceinline__ void collide_moments(const Phys<T>& ph, const SiteMom<T>& m, const T F[3], Out&& out)
+{
+    using L = Lat<LAT>;
+    constexpr int NP = L::NP;
+    const T rhoR = m.rr, sg = m.sg;
+    const T rho = ph.rho0 + sg;
+    const T rhoB = rho - rhoR;
+    const T inv_rho = T(1) / rho;
+    const T ux = m.jx * inv_rho, uy = m.jy * inv_rho, uz = L::D == 3 ? m.jz * inv_rho : T(0);
+    const T psi = (rhoR - rhoB) * inv_rho;
+
+    const T inv_nu = (T(1) + psi) * ph.half_inv_nu_r + (T(1) - psi) * ph.half_inv_nu_b;
+    const T tau = T(3) / inv_nu + T(0.5);
+    const T om1 = T(1) - T(1) / tau;
+
+    // equilibrium (Eqs. 6-7) as deviation from w_i rho0, even part per pair; its second
+    // moment is taken off Pi to leave Pi^neq
+    const T usq = ux * ux + uy * uy + uz * uz;
+    const T base = sg - T(1.5) * rho * usq;
+    const T dphi0 = rhoR * ph.dphiR[0] + rhoB * ph.dphiB[0];
+    const T dphi1 = rhoR * ph.dphiR[1] + rhoB * ph.dphiB[1];
+    const T dphi2 = rhoR * ph.dphiR[2] + rhoB * ph.dphiB[2];
+    const T eq0 = (T)L::w(0) * base + dphi0;
+    T qxx = m.pxx, qyy = m.pyy, qzz = m.pzz, qxy = m.pxy, qxz = m.pxz, qyz = m.pyz;
+    T eS[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int p = L::rep(k);
+        const int ax = L::cx(p), ay = L::cy(p), az = L::cz(p);
+        const T cu = (T)ax * ux + (T)ay * uy + (T)az * uz;
+        eS[k] = (T)L::w(p) * (base + T(4.5) * rho * cu * cu) + (L::cls(p) == 1 ? dphi1 : dphi2);
+        const T e = T(2) * eS[k];
+        if (ax) qxx -= e;
+        if (ay) qyy -= e;
+        if (az) qzz -= e;
+        if (ax && ay) qxy -= (ax * ay > 0) ? e : -e;
+        if (ax && az) qxz -= (ax * az > 0) ? e : -e;
+        if (ay && az) qyz -= (ay * az > 0) ? e : -e;
+    }
+    const T tr3 = (qxx + qyy + qzz) * (T(1) / T(3));
+    T g0 = eq0 + om1 * (T(4.5) * (T)L::w(0)) * (-tr3);
+
+    // perturbation (Eq. 9)
+    const T fn2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+    const bool has_f = fn2 > T(1e-20);
+    const T fn = has_f ? sqrt(fn2) : T(0);
+    const T inv_fn = has_f ? T(1) / fn : T(0);
+    const T inv_fn2 = inv_fn * inv_fn;
+    const T half_a_fn = T(0.5) * ph.A * fn;
+    if (has_f) g0 -= half_a_fn * (T)L::Bc(0);
+
+    // recolouring (Eq. 10); the rest direction takes rho_R minus the others
+    const T seg = ph.beta * rhoR * rhoB * inv_rho * inv_rho;
+    const T fracR = rhoR * inv_rho;
+    const T inv_sqrt2 = T(0.70710678118654752440);
+    const T ew1 = rhoR * ph.phiR[1] + rhoB * ph.phiB[1];
+    const T ew2 = rhoR * ph.phiR[2] + rhoB * ph.phiB[2];
+    T rsum = 0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int p = L::rep(k), q = L::opp(p);
+        const int ax = L::cx(p), ay = L::cy(p), az = L::cz(p);
+        const int c = L::cls(p);
+        T qp = -tr3;
+        if (ax) qp += qxx;
+        if (ay) qp += qyy;
+        if (az) qp += qzz;
+        if (ax && ay) qp += T(2 * ax * ay) * qxy;
+        if (ax && az) qp += T(2 * ax * az) * qxz;
+        if (ay && az) qp += T(2 * ay * az) * qyz;
+        const T cu = (T)ax * ux + (T)ay * uy + (T)az * uz;
+        T gS = eS[k] + om1 * (T(4.5) * (T)L::w(p)) * qp;
+        const T gA = (T(3) * (T)L::w(p)) * rho * cu;
+        const T fcs = (T)ax * F[0] + (T)ay * F[1] + (T)az * F[2];
+        if (has_f) gS += half_a_fn * ((T)L::w(p) * fcs * fcs * inv_fn2 - (T)L::Bc(p));
+        const T cosphi = c == 1 ? fcs * inv_fn : fcs * inv_fn * inv_sqrt2;
+        const T X = fracR * (gS + ph.wr0[c]);
+        const T Y = fracR * gA + seg * cosphi * (c == 1 ? ew1 : ew2);
+        const T rp = X + Y, rq = X - Y;
+        out(p, rp, gS + gA);
+        out(q, rq, gS - gA);
+        rsum += rp + rq;
+    }
+    out(0, rhoR - rsum, g0);
+}
+
 }  // namespace lbcg

@@ -142,6 +142,7 @@ namespace lbcg {
 
 // launchers (step.cu)
 cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b);
+int effective_variant(const lbcg_ctx* c);  // the step kernel variant launch_step runs
 // launchers (aux.cu)
 cudaError_t launch_fill_ports(lbcg_ctx* c, void* a);
 cudaError_t launch_init(lbcg_ctx* c, const double* rr, const double* rb, const double* u, void* a);

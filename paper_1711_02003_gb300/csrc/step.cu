@@ -22,6 +22,8 @@
 // Element offsets are 32-bit when all 2Q planes fit below 2^31 elements (IDX = int),
 // 64-bit otherwise.  Upstream offsets are site-index differences precomputed per
 // lane (x), row (y) and plane (z), so periodic wrap costs nothing per direction.
+#include <type_traits>
+
 #include "lbcg_device.cuh"
 
 namespace lbcg {
@@ -415,6 +417,221 @@ __global__ void __launch_bounds__(256, 3) k_step_d3q19_occ(const KParams P,
     int bx, by, bz;
     block_of(P, tiles, bx, by, bz);
     tile_d3q19<PREC, false, IDX>(P, A, B, link, bx, by, bz, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+}
+
+// ------------------------------------------------- moment march (variants 6, 7; regularized)
+template <typename T>
+__device__ __forceinline__ void mom_put(const SiteMom<T>& m, T* p, int st)
+{
+    p[0] = m.rr;
+    p[st] = m.sg;
+    p[2 * st] = m.jx;
+    p[3 * st] = m.jy;
+    p[4 * st] = m.jz;
+    p[5 * st] = m.pxx;
+    p[6 * st] = m.pyy;
+    p[7 * st] = m.pzz;
+    p[8 * st] = m.pxy;
+    p[9 * st] = m.pxz;
+    p[10 * st] = m.pyz;
+}
+
+template <typename T>
+__device__ __forceinline__ void mom_get(SiteMom<T>& m, const T* p, int st)
+{
+    m.rr = p[0];
+    m.sg = p[st];
+    m.jx = p[2 * st];
+    m.jy = p[3 * st];
+    m.jz = p[4 * st];
+    m.pxx = p[5 * st];
+    m.pyy = p[6 * st];
+    m.pzz = p[7 * st];
+    m.pxy = p[8 * st];
+    m.pxz = p[9 * st];
+    m.pyz = p[10 * st];
+}
+
+// Streamed populations of one fluid site summed into the moments of the regularized
+// collision as they arrive (pull, Eq. 1, halfway bounce-back on the link bits); returns
+// psi.  FULL = false: only rho_R and rho (psi of a ring site).
+template <int LAT, int PREC, typename IDX, bool FULL>
+__device__ __forceinline__ typename Store<PREC>::T pull_moments(const KParams& P,
+                                                                const typename Store<PREC>::S* __restrict__ A, IDX s,
+                                                                const Up& u, uint32_t lk,
+                                                                SiteMom<typename Store<PREC>::T>& m)
+{
+    using L = Lat<LAT>;
+    using SP = Store<PREC>;
+    using T = typename SP::T;
+    constexpr int Q = L::Q;
+    const IDX np = (IDX)P.np;
+    const Phys<T>& ph = phys<T>(P);
+    constexpr uint32_t qmask = (1u << Q) - 1u;
+    auto body = [&](auto walls) {
+        constexpr bool WALLS = decltype(walls)::value;
+        auto ld = [&](int i, T& r, T& g) {
+            IDX ir = (IDX)i * np + s + up_off<LAT, IDX>(u, i);
+            if (WALLS && ((lk >> i) & 1u)) ir = (IDX)L::opp(i) * np + s;
+            SP::load(A, ir, ir + (IDX)Q * np, ph, L::cls(i), r, g);
+        };
+        T r0, g0;
+        ld(0, r0, g0);
+        m.rr = r0;
+        m.sg = g0;
+#pragma unroll
+        for (int k = 0; k < L::NP; ++k) {
+            const int p = L::rep(k);
+            T rp, gp, rq, gq;
+            ld(p, rp, gp);
+            ld(L::opp(p), rq, gq);
+            mom_add_pair<LAT, FULL>(m, k, rp, gp, rq, gq);
+        }
+    };
+    if ((lk & qmask) == 0u)
+        body(std::false_type{});
+    else
+        body(std::true_type{});
+    const T rho = ph.rho0 + m.sg;
+    return (m.rr - (rho - m.rr)) / rho;
+}
+
+// The block tile of tile_d3q19, marching along z, with the waiting plane held as its
+// 11 moments: plane z+1 is pulled and summed (psi to the shared ring), then plane z
+// is collided from its moments and written.  No population is read twice from the
+// memory system and no population array lives in registers.  Regularized collision
+// only (the BGK update needs the individual populations).  MSMEM parks the waiting
+// moments in a thread-private shared-memory slot (two slots, alternating by plane)
+// instead of registers, for a smaller register budget.
+template <int PREC, typename IDX, bool MSMEM>
+__device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename Store<PREC>::S* __restrict__ A,
+                                               typename Store<PREC>::S* __restrict__ B,
+                                               const uint32_t* __restrict__ link, int bx, int by, int bz,
+                                               typename Store<PREC>::T* psi_s)
+{
+    using T = typename Store<PREC>::T;
+    using SP = Store<PREC>;
+    using L = Lat<1>;
+    constexpr int Q = 19;
+    const int lane = threadIdx.x;
+    const int w = threadIdx.y;
+    const int WY = blockDim.y;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const long long nxy = (long long)nx * ny;
+    const int x = bx * 30 + lane - 1;
+    const int y = by * (WY - 2) + w - 1;
+    int xs, ys;
+    const bool xok = wrap_coord(x, nx, P.per[0], xs) && x <= nx;
+    const bool yok = wrap_coord(y, ny, P.per[1], ys) && y <= ny;
+    const bool row_in = w >= 1 && w <= WY - 2 && y < ny;  // warp-uniform
+    const bool inner = row_in && lane >= 1 && lane <= 30 && x < nx;
+    Up u;
+    {
+        int a, b;
+        nbr_off(xs, nx, P.per[0], u.xm, u.xp);
+        nbr_off(ys, ny, P.per[1], a, b);
+        u.ym = (long long)a * nx;
+        u.yp = (long long)b * nx;
+    }
+    const IDX sxy = (IDX)xs + (IDX)nx * (IDX)ys;
+    const IDX np = (IDX)P.np;
+    const int z0 = bz * P.rows;
+    const int z1 = min(z0 + P.rows, nz);
+    const Phys<T>& ph = phys<T>(P);
+    const T psi_wall = ph.psi_wall;
+
+    SiteMom<T> mb;
+    mom_zero(mb);
+    bool coll_b = false;
+    T* const mom_s = psi_s + 4 * WY * 32 + (w * 32 + lane);  // [slot][11][WY * 32]
+    const int mstride = WY * 32;
+
+#pragma unroll 1
+    for (int zz = z0 - 1; zz <= z1; ++zz) {
+        int zs;
+        const bool zok = wrap_coord(zz, nz, P.per[2], zs);
+        {
+            int a, b;
+            nbr_off(zs, nz, P.per[2], a, b);
+            u.zm = (long long)a * nxy;
+            u.zp = (long long)b * nxy;
+        }
+        SiteMom<T> mn;
+        mom_zero(mn);
+        T psi_n = psi_wall;
+        bool fluid_n = false;
+        const IDX s = sxy + (IDX)nxy * (IDX)zs;
+        const bool full = row_in && zz >= z0 && zz < z1;  // block-uniform in z, warp-uniform in y
+        if (xok && yok && zok) {
+            const uint32_t lk = link ? __ldg(link + s) : 0u;
+            const uint32_t type = (lk >> kTypeShift) & 3u;
+            if (type == kTypeFluid) {
+                psi_n = full ? pull_moments<1, PREC, IDX, true>(P, A, s, u, lk, mn)
+                             : pull_moments<1, PREC, IDX, false>(P, A, s, u, lk, mn);
+                fluid_n = true;
+            } else if (type == kTypePort) {
+                psi_n = ghost_psi<1, PREC, IDX>(P, A, s);
+            }
+        }
+        const int slot_n = (zz - z0 + 1) & 3;
+        psi_s[(slot_n * WY + w) * 32 + lane] = psi_n;
+        if (MSMEM && fluid_n && full) mom_put(mn, mom_s + (zz & 1) * 11 * mstride, mstride);
+        __syncthreads();
+        if (zz - 1 >= z0 && coll_b) {
+            const int zc = zz - 1;
+            const IDX sc = sxy + (IDX)nxy * (IDX)zc;
+            auto nb = [&](int cx, int cy, int cz) -> T {
+                const int slot = (zc + cz - z0 + 1) & 3;
+                return psi_s[(slot * WY + (w + cy)) * 32 + (lane + cx)];
+            };
+            T F[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int k = 0; k < L::NP; ++k) {
+                const int p = L::rep(k);
+                const int cx = L::cx(p), cy = L::cy(p), cz = L::cz(p);
+                const T d = (T)L::w(p) * (nb(cx, cy, cz) - nb(-cx, -cy, -cz));
+                if (cx) F[0] += cx > 0 ? d : -d;
+                if (cy) F[1] += cy > 0 ? d : -d;
+                if (cz) F[2] += cz > 0 ? d : -d;
+            }
+            F[0] *= T(3);
+            F[1] *= T(3);
+            F[2] *= T(3);
+            if (MSMEM) mom_get(mb, mom_s + (zc & 1) * 11 * mstride, mstride);
+            collide_moments<1, T>(ph, mb, F, [&](int i, T r, T g) {
+                const IDX ir = (IDX)i * np + sc;
+                SP::store(B, ir, ir + (IDX)Q * np, ph, L::cls(i), r, g);
+            });
+        }
+        coll_b = fluid_n && inner && zz >= z0 && zz < z1;
+        if (!MSMEM) mb = mn;
+    }
+}
+
+template <int PREC, typename IDX>
+__global__ void __launch_bounds__(256, 3) k_step_d3q19_mom(const KParams P,
+                                                           const typename Store<PREC>::S* __restrict__ A,
+                                                           typename Store<PREC>::S* __restrict__ B,
+                                                           const uint32_t* __restrict__ link, const int* __restrict__ tiles)
+{
+    extern __shared__ unsigned char smem_raw[];
+    int bx, by, bz;
+    block_of(P, tiles, bx, by, bz);
+    tile_d3q19_mom<PREC, IDX, false>(P, A, B, link, bx, by, bz, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+}
+
+// variant 7: the moment march with the waiting moments in shared memory; 64 registers, so
+// four blocks of 8 warps or two of 16 per SM
+template <int PREC, typename IDX>
+__global__ void __launch_bounds__(512, 2) k_step_d3q19_moms(const KParams P,
+                                                            const typename Store<PREC>::S* __restrict__ A,
+                                                            typename Store<PREC>::S* __restrict__ B,
+                                                            const uint32_t* __restrict__ link, const int* __restrict__ tiles)
+{
+    extern __shared__ unsigned char smem_raw[];
+    int bx, by, bz;
+    block_of(P, tiles, bx, by, bz);
+    tile_d3q19_mom<PREC, IDX, true>(P, A, B, link, bx, by, bz, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
 }
 
 // ------------------------------------------------- pipelined variants (variant 3)
@@ -859,10 +1076,12 @@ __global__ void __launch_bounds__(256) k_batch_d2q9(const BatchSlot* __restrict_
     }
 }
 
-template <int PREC, bool KEEP>
-__global__ void __launch_bounds__(256, 2) k_batch_d3q19(const BatchSlot* __restrict__ slots,
-                                                        const BatchItem* __restrict__ items,
-                                                        const int* __restrict__ nitems, int k)
+// Regularized instances take the moment march (moments in registers), BGK instances the
+// re-read march; MINB resident blocks per SM (3; FP64 2)
+template <int PREC, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_batch_d3q19(const BatchSlot* __restrict__ slots,
+                                                           const BatchItem* __restrict__ items,
+                                                           const int* __restrict__ nitems, int k)
 {
     using S = typename Store<PREC>::S;
     using T = typename Store<PREC>::T;
@@ -879,7 +1098,10 @@ __global__ void __launch_bounds__(256, 2) k_batch_d3q19(const BatchSlot* __restr
         const bool odd = k & 1;
         const S* src = (const S*)(odd ? sl.b : sl.a);
         S* dst = (S*)(odd ? sl.a : sl.b);
-        tile_d3q19<PREC, KEEP, int>(sP, src, dst, sl.link, it.x, it.y, it.z, reinterpret_cast<T*>(smem_raw));
+        if (sP.collision == LBCG_REG)
+            tile_d3q19_mom<PREC, int, false>(sP, src, dst, sl.link, it.x, it.y, it.z, reinterpret_cast<T*>(smem_raw));
+        else
+            tile_d3q19<PREC, false, int>(sP, src, dst, sl.link, it.x, it.y, it.z, reinterpret_cast<T*>(smem_raw));
     }
 }
 
@@ -896,23 +1118,17 @@ cudaError_t launch_batch_step(int lattice, int precision, const BatchSlot* slots
             default: k_batch_d2q9<LBCG_FP16_SCALED><<<grid, 256, 0, st>>>(slots, items, nitems, k); break;
         }
     } else {
-        const unsigned grid = sms * 2;
         const dim3 block(32, 8);
+        const size_t sm4 = 4 * 8 * 32 * sizeof(float);
         switch (precision) {
             case LBCG_FP64:
-                k_batch_d3q19<LBCG_FP64, false><<<grid, block, 4 * 8 * 32 * sizeof(double), st>>>(slots, items, nitems, k);
+                k_batch_d3q19<LBCG_FP64, 2><<<sms * 2, block, 4 * 8 * 32 * sizeof(double), st>>>(slots, items, nitems, k);
                 break;
-            case LBCG_FP32:
-                k_batch_d3q19<LBCG_FP32, true><<<grid, block, 4 * 8 * 32 * sizeof(float), st>>>(slots, items, nitems, k);
-                break;
+            case LBCG_FP32: k_batch_d3q19<LBCG_FP32, 3><<<sms * 3, block, sm4, st>>>(slots, items, nitems, k); break;
             case LBCG_FP32_DEV:
-                k_batch_d3q19<LBCG_FP32_DEV, true><<<grid, block, 4 * 8 * 32 * sizeof(float), st>>>(slots, items,
-                                                                                                nitems, k);
+                k_batch_d3q19<LBCG_FP32_DEV, 3><<<sms * 3, block, sm4, st>>>(slots, items, nitems, k);
                 break;
-            default:
-                k_batch_d3q19<LBCG_FP16_SCALED, true><<<grid, block, 4 * 8 * 32 * sizeof(float), st>>>(slots, items,
-                                                                                                   nitems, k);
-                break;
+            default: k_batch_d3q19<LBCG_FP16_SCALED, 3><<<sms * 3, block, sm4, st>>>(slots, items, nitems, k); break;
         }
     }
     return cudaGetLastError();
@@ -972,6 +1188,25 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant
             return cudaGetLastError();
         }
     }
+    if (variant == 7 && !KEEP) {
+        const size_t smem7 = smem + 2 * 11 * (size_t)wy * 32 * sizeof(T);
+        if (small_index(c)) {
+            cudaFuncSetAttribute(k_step_d3q19_moms<PREC, int>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem7);
+            k_step_d3q19_moms<PREC, int><<<grid, block, smem7, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+        } else {
+            cudaFuncSetAttribute(k_step_d3q19_moms<PREC, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem7);
+            k_step_d3q19_moms<PREC, long long><<<grid, block, smem7, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+        }
+        return cudaGetLastError();
+    }
+    if (variant == 6 && !KEEP) {
+        if (small_index(c))
+            k_step_d3q19_mom<PREC, int><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+        else
+            k_step_d3q19_mom<PREC, long long><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+        return cudaGetLastError();
+    }
     if (variant == 5 && !KEEP) {
         if (small_index(c))
             k_step_d3q19_occ<PREC, int><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
@@ -998,6 +1233,20 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant
     return cudaGetLastError();
 }
 
+int effective_variant(const lbcg_ctx* c)
+{
+    const int prec = c->p.precision;
+    if (c->p.lattice == LBCG_D2Q9) return c->variant == 3 ? 3 : 0;
+    // default (measured fastest): the moment march, with its moments in shared memory for
+    // 4- and 2-byte storage and in registers for FP64; the BGK update needs the individual
+    // populations and re-reads them (three blocks per SM, FP64 two)
+    const bool reg = c->p.collision == LBCG_REG;
+    int v = c->variant != 0 ? c->variant : (reg ? (prec == LBCG_FP64 ? 6 : 7) : (prec == LBCG_FP64 ? 2 : 5));
+    if ((v == 6 || v == 7) && !reg) v = prec == LBCG_FP64 ? 2 : 5;
+    if (v == 4 && prec != LBCG_FP32 && prec != LBCG_FP32_DEV) v = 2;
+    return v;
+}
+
 cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b)
 {
     const int prec = c->p.precision;
@@ -1011,7 +1260,7 @@ cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b)
     } else {
         // default: 5 (re-read, three blocks per SM; measured fastest) for 4- and 2-byte storage;
         // FP64 re-reads with two blocks per SM (it spills at the three-block register budget)
-        const int v = c->variant != 0 ? c->variant : (prec == LBCG_FP64 ? 2 : 5);
+        const int v = effective_variant(c);
         const bool keep = v == 1;
         switch (prec) {
             case LBCG_FP64:

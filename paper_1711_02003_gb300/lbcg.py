@@ -57,6 +57,7 @@ class LbcgError(RuntimeError):
 _lib = None
 _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
 _PROTOS = {
     "lbcg_strerror": (C.c_char_p, [C.c_int]),
     "lbcg_last_error": (C.c_char_p, []),
@@ -86,6 +87,7 @@ _PROTOS = {
     "lbcg_set_kernel_timing": (C.c_int, [_vp, C.c_int]),
     "lbcg_kernel_time": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong)]),
     "lbcg_set_launch": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
+    "lbcg_get_launch": (C.c_int, [_vp, _ip, _ip, _ip]),
     "lbcg_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp)]),
     "lbcg_batch_destroy": (None, [_vp]),
     "lbcg_batch_add": (C.c_int, [_vp, _vp, C.c_longlong, C.POINTER(C.c_int)]),
@@ -199,6 +201,13 @@ class Simulation:
     # ---------------------------------------------------------------- calls
     def set_launch(self, rows: int = 0, block_rows: int = 0, variant: int = 0):
         _check("lbcg_set_launch", _lib.lbcg_set_launch(self._h, int(rows), int(block_rows), int(variant)))
+
+    @property
+    def launch(self) -> dict:
+        """The launch shape in use after defaults: rows, block_rows, variant."""
+        r, b, v = C.c_int(), C.c_int(), C.c_int()
+        _check("lbcg_get_launch", _lib.lbcg_get_launch(self._h, C.byref(r), C.byref(b), C.byref(v)))
+        return {"rows": r.value, "block_rows": b.value, "variant": v.value}
 
     def init_fields(self, rho_r, rho_b, u=None):
         rr = np.ascontiguousarray(rho_r, np.float64).ravel()

@@ -390,3 +390,24 @@ def serving_problem(spec: dict, A: float = 0.01, tau_cont: float = 1.0) -> Probl
             pb = step_emulsifier(nx, ny, nz, terrace_len=max(4, nx // 3), terrace_h=max(2, nz // 4), u_in=U,
                                  tau_cont=tau_cont, tau_disp=tau_d, A=A, fill_x=max(2, nx // 6), seed=spec["seed"])
     return pb.replace(name=f"request {spec['seed']}: {pb.name}, Ca {spec['ca']:.2e}, ratio {spec['visc_ratio']:.2f}")
+
+
+# Named single-instance workloads (benchmark and profiling runs): name -> (problem,
+# description, a site inside the dispersed phase for the observables)
+NAMED = ("step_emulsifier", "flow_focuser", "droplet2d", "droplet3d")
+
+
+def named(name: str):
+    if name == "step_emulsifier":
+        return (step_emulsifier(), "3D step emulsifier D3Q19 768x128x32 (terrace 256x126x8, reservoir 512x126x30)",
+                (384, 64, 16))
+    if name == "flow_focuser":
+        return (cross_junction(), "2D flow-focusing cross junction D2Q9 1024x192 (main channel 64, side inlets 64 "
+                "at x=256)", (512, 96))
+    if name == "droplet2d":
+        return static_droplet(D2Q9, 4096, 512), "2D static droplet D2Q9 4096x4096 periodic, R=512", (2048, 2048)
+    if name == "droplet3d":
+        c = (127.5, 127.5, 127.5)
+        return (static_droplet(D3Q19, 256, 64, centre=c), "3D static droplet D3Q19 256^3 periodic, R=64 (off-site "
+                "centre)", c)
+    raise ValueError(f"unknown workload {name}; known: {', '.join(NAMED)}")

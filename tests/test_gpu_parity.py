@@ -119,7 +119,8 @@ def test_fp64_d3q19_step_emulsifier():
 # variants (registers / re-read / pipelined) may contract multiply-adds differently, so they
 # are held to rounding level.
 @pytest.mark.parametrize("rows,block_rows,variant", [(1, 3, 0), (5, 7, 0), (64, 8, 0), (5, 7, 1), (64, 8, 2), (3, 4, 4), (8, 8, 4),
-                                                     (3, 5, 3), (8, 8, 3), (8, 8, 5), (3, 6, 5)])
+                                                     (3, 5, 3), (8, 8, 3), (8, 8, 5), (3, 6, 5), (8, 8, 6), (3, 5, 6),
+                                                     (8, 8, 7), (5, 4, 7)])
 def test_launch_shape_does_not_change_results(rows, block_rows, variant):
     lb = _lb()
     pb = W.step_emulsifier(nx=50, ny=30, nz=10, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10)
