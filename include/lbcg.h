@@ -293,8 +293,15 @@ int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
  * memory ring, 5 (D3Q19) re-read compiled for three resident blocks per SM,
  * 6 (D3Q19, regularized) moment march: the waiting plane is held as the 11 moments the
  * regularized collision needs (Eq. 11 rebuilds every population from them), so nothing
- * is read twice, 7 the same with those moments in shared memory (64 registers).
- * Variants 6 and 7 fall back to 5 (FP64: 2) for the BGK collision.  The default is the
+ * is read twice, 7 the same with those moments in shared memory (64 registers),
+ * 8 (D3Q19, regularized, FP32 or FP32-dev storage, nx a multiple of 4, block_rows 6 or
+ * 8) the moment march with every plane's pulled populations staged in shared memory by
+ * the tensor memory accelerator (two-stage pipeline of Q boxes per plane, bounded
+ * waits); where its conditions do not hold it runs as 7 (FP64: 6).  Variants 6 and 7
+ * fall back to 5 (FP64: 2) for the BGK collision.  A context created while the
+ * environment variable LBCG_TEST_PIPELINE_STALL=1 is set makes every pipeline wait of
+ * variant 8 run out (failure-path test): the step then leaves the state invalid and
+ * lbcg_synchronize and the read-back calls report LBCG_ERR_CUDA once.  The default is the
  * plain march for D2Q9; for D3Q19 with the regularized collision variant 7 (FP64: 6),
  * with BGK variant 5 (FP64: 2).  Within one variant results are bit-identical across
  * shapes; variants may contract multiply-adds and order sums differently and agree to

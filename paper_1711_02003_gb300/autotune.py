@@ -10,7 +10,8 @@ Candidates:
   D2Q9 : rows per warp strip in {8, 16, 32, 64} x variant {0 plain march, 3 pipelined}
   D3Q19: warps per block along y in {4, 6, 8} x z-planes per block in {4, 8, 16} x
          variant; regularized collision {7, 6 moment march (shared-memory / register
-         moments), 5 re-read}, plus 12 and 16 warps per block for variant 7; BGK
+         moments), 5 re-read}, plus 12 and 16 warps per block for variant 7 and the
+         TMA-staged march (variant 8; 6 or 8 warps, 8 or 16 planes) for 4-byte storage; BGK
          {5, 1, 2, 4 (4-byte storage only)}; FP64 regularized {6, 2}, BGK {2, 1}
 
 Run as a program it prints the candidate table of one named workload, in launch order
@@ -40,6 +41,8 @@ def candidates(lattice: int, precision: int, collision: int = 0) -> list:
     out = [dict(rows=r, block_rows=b, variant=v) for v, b, r in itertools.product(variants, (4, 6, 8), (4, 8, 16))]
     if 7 in variants:
         out += [dict(rows=r, block_rows=b, variant=7) for b, r in itertools.product((12, 16), (4, 8))]
+        if lbcg.ELEM_BYTES[precision] == 4:  # TMA-staged march (runs as 7 where it does not apply)
+            out += [dict(rows=r, block_rows=b, variant=8) for b, r in itertools.product((6, 8), (8, 16))]
     return out
 
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -167,6 +168,7 @@ void fill_kparams(lbcg_ctx* c)
 {
     if (c->p.lattice != LBCG_D2Q9 && c->block_rows <= 2) c->block_rows = 8;
     c->kp = make_kparams(c->p, c->dims, c->np, c->rows, c->block_rows);
+    c->kp.stall_test = c->stall_test;
     c->kp.ntiles = c->d_tiles ? c->ntiles : 0;
 }
 
@@ -272,7 +274,17 @@ int lbcg_create(const lbcg_params* p, void* stream, lbcg_ctx** out)
     c->n = sites_of(&c->p);
     c->np = padded(c->n);
     c->state_bytes = (size_t)2 * c->Q * c->np * elem_size(c->p.precision);
+    {
+        const char* t = std::getenv("LBCG_TEST_PIPELINE_STALL");
+        c->stall_test = t && t[0] == '1';
+    }
     fill_kparams(c);
+    // status word of the bounded pipeline waits in the TMA-staged step kernel
+    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return fail(LBCG_ERR_NOMEM, "status word allocation failed");
+    }
     *out = c;
     return LBCG_OK;
 }
@@ -288,6 +300,7 @@ void lbcg_destroy(lbcg_ctx* c)
     cudaFree(c->d_scratch);
     cudaFree(c->d_partials);
     cudaFree(c->d_result);
+    cudaFree(c->d_status);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
@@ -651,11 +664,23 @@ int lbcg_step(lbcg_ctx* c, long long nsteps)
 
 long long lbcg_step_count(const lbcg_ctx* c) { return c ? c->step : -1; }
 
+// After a synchronisation: a step kernel whose shared-memory pipeline wait timed out left
+// a nonzero status word (its results are invalid); report it once and clear it.
+static int check_status(lbcg_ctx* c)
+{
+    if (!c->d_status) return LBCG_OK;
+    int h = 0;
+    LBCG_CUDA(cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+    if (h == 0) return LBCG_OK;
+    LBCG_CUDA(cudaMemset(c->d_status, 0, sizeof(int)), "status reset");
+    return fail(LBCG_ERR_CUDA, "step kernel: a shared-memory pipeline wait timed out; the state is invalid");
+}
+
 int lbcg_synchronize(lbcg_ctx* c)
 {
     if (!c) return fail(LBCG_ERR_ARG, "null context");
     LBCG_CUDA(cudaStreamSynchronize(c->stream), "stream sync");
-    return LBCG_OK;
+    return check_status(c);
 }
 
 int lbcg_get_fields_device(lbcg_ctx* c, double* rr, double* rb, double* u)
@@ -682,6 +707,7 @@ int lbcg_get_fields(lbcg_ctx* c, double* rr, double* rb, double* u)
     LBCG_CUDA(cudaMemcpyAsync(rb, stg + n, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy rho_b");
     LBCG_CUDA(cudaMemcpyAsync(u, stg + 2 * n, n * 8 * c->D, cudaMemcpyDeviceToHost, c->stream), "copy u");
     LBCG_CUDA(cudaStreamSynchronize(c->stream), "fields sync");
+    if (const int st_ = check_status(c)) return st_;
     return LBCG_OK;
 }
 
@@ -703,7 +729,7 @@ int lbcg_get_populations(lbcg_ctx* c, double* f)
                       "copy populations");
             LBCG_CUDA(cudaStreamSynchronize(c->stream), "populations sync");
         }
-    return LBCG_OK;
+    return check_status(c);
 }
 
 int lbcg_set_populations(lbcg_ctx* c, const double* f)
@@ -737,6 +763,7 @@ int lbcg_get_state(lbcg_ctx* c, void* host, size_t bytes)
     if (!host || bytes != c->state_bytes) return fail(LBCG_ERR_ARG, "host buffer must be lbcg_state_bytes long");
     LBCG_CUDA(cudaMemcpyAsync(host, c->A, bytes, cudaMemcpyDeviceToHost, c->stream), "copy state");
     LBCG_CUDA(cudaStreamSynchronize(c->stream), "state sync");
+    if (const int st_ = check_status(c)) return st_;
     return LBCG_OK;
 }
 
@@ -749,6 +776,7 @@ int lbcg_set_state(lbcg_ctx* c, const void* host, size_t bytes)
     st = mirror_state(c);
     if (st) return st;
     LBCG_CUDA(cudaStreamSynchronize(c->stream), "state sync");
+    if (const int st_ = check_status(c)) return st_;
     c->fields = true;
     return LBCG_OK;
 }
@@ -817,6 +845,7 @@ int lbcg_observables(lbcg_ctx* c, const double centre[3], double r_in, double r_
     double res[2 * kObsSlots];
     LBCG_CUDA(cudaMemcpyAsync(res, c->d_result, sizeof(res), cudaMemcpyDeviceToHost, c->stream), "copy result");
     LBCG_CUDA(cudaStreamSynchronize(c->stream), "observables sync");
+    if (const int st_ = check_status(c)) return st_;
     std::memset(out, 0, sizeof(*out));
     out->mass_r = res[0];
     out->mass_b = res[1];
@@ -870,6 +899,7 @@ int lbcg_label(lbcg_ctx* c, int32_t* labels, int64_t* counts, double* volumes, i
     LBCG_CUDA(cudaMemcpyAsync(h.data(), half, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy volumes");
     LBCG_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy flag");
     LBCG_CUDA(cudaStreamSynchronize(c->stream), "label sync");
+    if (const int st_ = check_status(c)) return st_;
     if (hflag) return fail(LBCG_ERR_CUDA, "labelling iteration bound reached");
     // per-droplet count and volume in label order, sums in site order
     std::vector<int> slot(n, -1);
@@ -938,9 +968,9 @@ int lbcg_set_launch(lbcg_ctx* c, int rows, int block_rows, int variant)
     // blocks of up to 512 threads; every other kernel up to 256
     const int max_wy = variant == 7 && c->p.collision == LBCG_REG ? 16 : 8;
     if (rows < 0 || block_rows < 0 || (block_rows > 0 && (block_rows < 3 || block_rows > max_wy)) || variant < 0 ||
-        variant > 7)
+        variant > 8)
         return fail(LBCG_ERR_ARG,
-                    "launch shape out of range (block_rows in 3..8, 3..16 with variant 7; variant in 0..7)");
+                    "launch shape out of range (block_rows in 3..8, 3..16 with variant 7; variant in 0..8)");
     c->rows = rows;
     c->block_rows = block_rows;
     c->variant = variant;

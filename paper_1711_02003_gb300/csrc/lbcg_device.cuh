@@ -111,6 +111,13 @@ struct StorePlain {
         b[ir] = (S)r;
         b[ig] = (S)((g + ph.wr0[c]) - r);
     }
+    // register form of the two stored values of one direction (as load)
+    __device__ static __forceinline__ void decode(S fr_, S fb_, const Phys<T>& ph, int c, T& r, T& g)
+    {
+        const T fr = (T)fr_, fb = (T)fb_;
+        r = fr;
+        g = (fr + fb) - ph.wr0[c];
+    }
 };
 
 template <>
@@ -134,6 +141,11 @@ struct Store<LBCG_FP32_DEV> {
     {
         b[ir] = r;
         b[ig] = g;
+    }
+    __device__ static __forceinline__ void decode(S fr, S fg, const Phys<T>&, int, T& r, T& g)
+    {
+        r = fr;
+        g = fg;
     }
 };
 

@@ -43,6 +43,7 @@ struct KParams {
     int rows;               // marching length per warp / block
     int nsx, nsy, nsz;      // strips / blocks per axis
     int ntiles;             // entries of the active-tile list (0: launch every tile)
+    int stall_test;         // failure-path test: TMA pipeline waits cannot complete (short limit)
     Phys<float> pf;
     Phys<double> pd;
     double alpha_r, alpha_b;
@@ -68,7 +69,7 @@ struct BatchSlot {
     int steps;               // steps this launch advances the instance (0 = idle)
 };
 // work item: D2Q9 (slot, first strip, strip count <= 8, -); D3Q19 (slot, bx, by, bz);
-// port refill (slot, first ghost, ghost count <= 4, -)
+// port refill (slot, first ghost, ghost count <= 64, -)
 struct BatchItem {
     int slot, x, y, z;
 };
@@ -135,6 +136,15 @@ struct lbcg_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     void* graph_start[2] = {nullptr, nullptr};
 
+    // TMA-staged step kernel: tensor maps of the two state buffers (CUtensorMap, 128 bytes,
+    // encoded on first use for the buffer and block height they describe) and a device
+    // status word its bounded pipeline waits set on timeout
+    alignas(64) unsigned char tmap[2][128] = {};
+    const void* tmap_buf[2] = {nullptr, nullptr};
+    int tmap_wy[2] = {0, 0};
+    int* d_status = nullptr;
+    int stall_test = 0;  // LBCG_TEST_PIPELINE_STALL set when the context was created
+
     lbcg::KParams kp;
 };
 
@@ -143,6 +153,7 @@ namespace lbcg {
 // launchers (step.cu)
 cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b);
 int effective_variant(const lbcg_ctx* c);  // the step kernel variant launch_step runs
+bool tma_supported(const lbcg_ctx* c);     // the TMA-staged variant applies to this context
 // launchers (aux.cu)
 cudaError_t launch_fill_ports(lbcg_ctx* c, void* a);
 cudaError_t launch_init(lbcg_ctx* c, const double* rr, const double* rb, const double* u, void* a);

@@ -22,6 +22,10 @@
 // Element offsets are 32-bit when all 2Q planes fit below 2^31 elements (IDX = int),
 // 64-bit otherwise.  Upstream offsets are site-index differences precomputed per
 // lane (x), row (y) and plane (z), so periodic wrap costs nothing per direction.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 #include <type_traits>
 
 #include "lbcg_device.cuh"
@@ -624,14 +628,306 @@ __global__ void __launch_bounds__(256, 3) k_step_d3q19_mom(const KParams P,
 // four blocks of 8 warps or two of 16 per SM
 template <int PREC, typename IDX>
 __global__ void __launch_bounds__(512, 2) k_step_d3q19_moms(const KParams P,
-                                                            const typename Store<PREC>::S* __restrict__ A,
-                                                            typename Store<PREC>::S* __restrict__ B,
-                                                            const uint32_t* __restrict__ link, const int* __restrict__ tiles)
+                                                                const typename Store<PREC>::S* __restrict__ A,
+                                                                typename Store<PREC>::S* __restrict__ B,
+                                                                const uint32_t* __restrict__ link,
+                                                                const int* __restrict__ tiles)
 {
     extern __shared__ unsigned char smem_raw[];
     int bx, by, bz;
     block_of(P, tiles, bx, by, bz);
     tile_d3q19_mom<PREC, IDX, true>(P, A, B, link, bx, by, bz, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+}
+
+// ------------------------------------------- TMA-staged moment march (variant 8)
+// The moment march of tile_d3q19_mom with its pulls served from shared memory.  For every
+// pulled plane, warp 0 of the block asks the tensor memory accelerator for Q boxes, one
+// per direction holding both of its arrays: the 36 x WY floats the block's threads pull,
+// the rows and the plane already shifted by the direction's c_y and c_z, the x-range
+// starting at the 16-byte boundary at or below the shifted first lane.  Two stages: the boxes of
+// plane z+2 load while plane z+1 is summed and plane z collided.  A thread reads its 2Q
+// pulled values at fixed shared-memory offsets: no per-load address arithmetic and no
+// global-load latency of its own.  Global loads remain only where a box cannot serve the
+// pull: bounce-back links (the site's own opposite population) and upstream sites across
+// a periodic x or y edge (a box does not wrap; its out-of-range part is zero-filled and
+// never read).  Every pipeline wait is bounded: on timeout the block records it in the
+// status word, waits (bounded) for its copies in flight and returns.  Requirements: 4-byte
+// storage, regularized collision, nx a multiple of 4 (row stride a multiple of 16 bytes),
+// 32-bit element offsets.
+
+constexpr int kTmaBoxX = 36;            // floats per staged row: 32 lanes + up to 3 of shift
+constexpr int kTmaWaitLimit = 1 << 22;  // mbarrier polls before a wait gives up
+constexpr int kTmaStallLimit = 1 << 12; // the same in the failure-path test
+
+template <int WY>
+struct TmaLayout {
+    static constexpr int ROWS = kTmaBoxX * WY;             // floats of one array's rows
+    static constexpr int BOX = 2 * ROWS * 4;               // bytes of one box: both arrays
+    static constexpr int SLOT = (BOX + 127) / 128 * 128;   // 128-byte aligned box slot
+    static constexpr int SLOTF = SLOT / 4;                 // floats per slot
+    static constexpr int STAGE = 19 * SLOT;                // the Q boxes of one plane
+    static constexpr int PSI = 4 * WY * 32 * 4;            // psi ring
+    static constexpr int BYTES = 2 * STAGE + PSI + 16;     // + two mbarriers
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+// bounded wait for the phase with the given parity to complete; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit)
+{
+    for (int k = 0; k < limit; ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
+                                            int i, int k)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(i), "r"(k), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Pulled populations of one fluid site from the staged boxes (global loads where a box
+// cannot serve the pull), summed into the moments as in pull_moments; returns psi.
+template <int PREC, int WY, bool FULL>
+__device__ __forceinline__ float pull_staged(const KParams& P, const float* __restrict__ box,
+                                             const typename Store<PREC>::S* __restrict__ A, int s, const Up& u,
+                                             uint32_t lk, bool edge, int x, int y, const int (&sh)[3],
+                                             SiteMom<float>& m)
+{
+    using L = Lat<1>;
+    using SP = Store<PREC>;
+    constexpr int Q = 19;
+    constexpr int SF = TmaLayout<WY>::SLOTF;
+    const int np = (int)P.np;
+    const Phys<float>& ph = phys<float>(P);
+    constexpr uint32_t qmask = (1u << Q) - 1u;
+    auto body = [&](auto careful) {
+        constexpr bool CAREFUL = decltype(careful)::value;
+        auto ld = [&](int i, float& r, float& g) {
+            if (CAREFUL) {
+                const bool bounce = (lk >> i) & 1u;
+                const bool wrap = (P.per[0] && (unsigned)(x - L::cx(i)) >= (unsigned)P.nx) ||
+                                  (P.per[1] && (unsigned)(y - L::cy(i)) >= (unsigned)P.ny);
+                if (bounce || wrap) {
+                    const int ir = bounce ? L::opp(i) * np + s : i * np + s + up_off<1, int>(u, i);
+                    SP::load(A, ir, ir + Q * np, ph, L::cls(i), r, g);
+                    return;
+                }
+            }
+            const float* b = box + i * SF + sh[L::cx(i) + 1];
+            SP::decode(b[0], b[TmaLayout<WY>::ROWS], ph, L::cls(i), r, g);
+        };
+        float r0, g0;
+        ld(0, r0, g0);
+        m.rr = r0;
+        m.sg = g0;
+#pragma unroll
+        for (int k = 0; k < L::NP; ++k) {
+            const int p = L::rep(k);
+            float rp, gp, rq, gq;
+            ld(p, rp, gp);
+            ld(L::opp(p), rq, gq);
+            mom_add_pair<1, FULL>(m, k, rp, gp, rq, gq);
+        }
+    };
+    if ((lk & qmask) == 0u && !edge)
+        body(std::false_type{});
+    else
+        body(std::true_type{});
+    const float rho = ph.rho0 + m.sg;
+    return (m.rr - (rho - m.rr)) / rho;
+}
+
+template <int PREC, int WY>
+__device__ __forceinline__ void tile_d3q19_tma(const KParams& P, const CUtensorMap* map,
+                                               const typename Store<PREC>::S* __restrict__ A,
+                                               typename Store<PREC>::S* __restrict__ B,
+                                               const uint32_t* __restrict__ link, int bx, int by, int bz,
+                                               unsigned char* smem, int* status)
+{
+    using T = float;
+    using SP = Store<PREC>;
+    using L = Lat<1>;
+    using Lay = TmaLayout<WY>;
+    constexpr int Q = 19;
+    const int lane = threadIdx.x;
+    const int w = threadIdx.y;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const int nxy = nx * ny;
+    const int x0 = bx * 30 - 1, y0 = by * (WY - 2) - 1;  // lane 0 / warp 0 coordinates
+    const int x = x0 + lane, y = y0 + w;
+    int xs, ys;
+    const bool xok = wrap_coord(x, nx, P.per[0], xs) && x <= nx;
+    const bool yok = wrap_coord(y, ny, P.per[1], ys) && y <= ny;
+    const bool row_in = w >= 1 && w <= WY - 2 && y < ny;  // warp-uniform
+    const bool inner = row_in && lane >= 1 && lane <= 30 && x < nx;
+    const bool edge = (P.per[0] && (x <= 0 || x >= nx - 1)) || (P.per[1] && (y <= 0 || y >= ny - 1));
+    Up u;
+    {
+        int a, b;
+        nbr_off(xs, nx, P.per[0], u.xm, u.xp);
+        nbr_off(ys, ny, P.per[1], a, b);
+        u.ym = (long long)a * nx;
+        u.yp = (long long)b * nx;
+    }
+    const int sxy = xs + nx * ys;
+    const int np = (int)P.np;
+    const int z0 = bz * P.rows;
+    const int z1 = min(z0 + P.rows, nz);
+    const int nplanes = z1 - z0 + 2;  // pulled planes z0-1 .. z1
+    const Phys<T>& ph = phys<T>(P);
+    const T psi_wall = ph.psi_wall;
+    // column shift of a lane's pull inside a box, by c_x (box start: 16-byte boundary)
+    int sh[3];
+#pragma unroll
+    for (int c = -1; c <= 1; ++c) sh[c + 1] = (x0 - c) - ((x0 - c) & ~3);
+
+    T* psi_s = reinterpret_cast<T*>(smem + 2 * Lay::STAGE);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * Lay::STAGE + Lay::PSI);
+    if (lane == 0 && w == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // failure-path test: every phase expects 16 bytes that never come, so each wait runs out
+    const int wait_limit = P.stall_test ? kTmaStallLimit : kTmaWaitLimit;
+    const uint32_t extra_tx = P.stall_test ? 16u : 0u;
+    // warp 0: the Q boxes (both arrays of a direction each) of pulled plane p into stage k
+    auto issue = [&](int p, int k) {
+        if (lane == 0) mbar_expect_tx(&bar[k], Q * Lay::BOX + extra_tx);
+        __syncwarp();
+        if (lane < Q) {
+            const int i = lane;
+            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            int zsrc = p - cz;
+            if (P.per[2]) zsrc = zsrc < 0 ? zsrc + nz : (zsrc >= nz ? zsrc - nz : zsrc);
+            tma_load_5d(smem + k * Lay::STAGE + i * Lay::SLOT, map, &bar[k], (x0 - cx) & ~3, y0 - cy, zsrc, i, 0);
+        }
+    };
+    if (w == 0) {
+        issue(z0 - 1, 0);
+        issue(z0, 1);
+    }
+
+    SiteMom<T> mb;
+    mom_zero(mb);
+    bool coll_b = false;
+#pragma unroll 1
+    for (int k = 0; k < nplanes; ++k) {
+        const int zz = z0 - 1 + k;
+        const int stg = k & 1;
+        const bool got = mbar_wait(&bar[stg], (uint32_t)((k >> 1) & 1), wait_limit);
+        int zs;
+        const bool zok = wrap_coord(zz, nz, P.per[2], zs);
+        {
+            int a, b;
+            nbr_off(zs, nz, P.per[2], a, b);
+            u.zm = (long long)a * nxy;
+            u.zp = (long long)b * nxy;
+        }
+        SiteMom<T> mn;
+        mom_zero(mn);
+        T psi_n = psi_wall;
+        bool fluid_n = false;
+        const int s = sxy + nxy * zs;
+        const bool full = row_in && zz >= z0 && zz < z1;
+        if (got && xok && yok && zok) {
+            const uint32_t lk = link ? __ldg(link + s) : 0u;
+            const uint32_t type = (lk >> kTypeShift) & 3u;
+            if (type == kTypeFluid) {
+                const float* box = reinterpret_cast<const float*>(smem + stg * Lay::STAGE) + w * kTmaBoxX + lane;
+                psi_n = full ? pull_staged<PREC, WY, true>(P, box, A, s, u, lk, edge, x, y, sh, mn)
+                             : pull_staged<PREC, WY, false>(P, box, A, s, u, lk, edge, x, y, sh, mn);
+                fluid_n = true;
+            } else if (type == kTypePort) {
+                psi_n = ghost_psi<1, PREC, int>(P, A, s);
+            }
+        }
+        psi_s[(((k & 3) * WY) + w) * 32 + lane] = psi_n;
+        if (__syncthreads_or(!got)) {
+            // a copy did not arrive: record it, wait (bounded) for both stages, give up
+            if (lane == 0 && w == 0) atomicExch(status, 1);
+            mbar_wait(&bar[stg], (uint32_t)((k >> 1) & 1), wait_limit);
+            if (k + 1 < nplanes) mbar_wait(&bar[stg ^ 1], (uint32_t)(((k + 1) >> 1) & 1), wait_limit);
+            return;
+        }
+        // every thread is done with stage stg: refill it with plane zz + 2
+        if (w == 0 && k + 2 < nplanes) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(zz + 2, stg);
+        }
+        if (k >= 2 && coll_b) {
+            const int zc = zz - 1;
+            const int sc = sxy + nxy * zc;
+            auto nb = [&](int cx, int cy, int cz) -> T {
+                const int slot = (k - 1 + cz) & 3;
+                return psi_s[(slot * WY + (w + cy)) * 32 + (lane + cx)];
+            };
+            T F[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int kk = 0; kk < L::NP; ++kk) {
+                const int p = L::rep(kk);
+                const int cx = L::cx(p), cy = L::cy(p), cz = L::cz(p);
+                const T d = (T)L::w(p) * (nb(cx, cy, cz) - nb(-cx, -cy, -cz));
+                if (cx) F[0] += cx > 0 ? d : -d;
+                if (cy) F[1] += cy > 0 ? d : -d;
+                if (cz) F[2] += cz > 0 ? d : -d;
+            }
+            F[0] *= T(3);
+            F[1] *= T(3);
+            F[2] *= T(3);
+            collide_moments<1, T>(ph, mb, F, [&](int i, T r, T g) {
+                const int ir = i * np + sc;
+                SP::store(B, ir, ir + Q * np, ph, L::cls(i), r, g);
+            });
+        }
+        coll_b = fluid_n && inner && full;
+        mb = mn;
+    }
+}
+
+template <int PREC, int WY>
+__global__ void __launch_bounds__(32 * WY, WY <= 6 ? 3 : 2) k_step_d3q19_tma(const KParams P,
+                                                                              const __grid_constant__ CUtensorMap tmA,
+                                                                              const typename Store<PREC>::S* __restrict__ A,
+                                                                              typename Store<PREC>::S* __restrict__ B,
+                                                                              const uint32_t* __restrict__ link,
+                                                                              const int* __restrict__ tiles, int* status)
+{
+    extern __shared__ __align__(1024) unsigned char smem_tma[];
+    int bx, by, bz;
+    block_of(P, tiles, bx, by, bz);
+    tile_d3q19_tma<PREC, WY>(P, &tmA, A, B, link, bx, by, bz, smem_tma, status);
 }
 
 // ------------------------------------------------- pipelined variants (variant 3)
@@ -1161,6 +1457,85 @@ static cudaError_t launch_d2q9(lbcg_ctx* c, const void* a, void* b)
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------- tensor maps (host)
+static PFN_cuTensorMapEncodeTiled_v12000 tma_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+bool tma_supported(const lbcg_ctx* c)
+{
+    const int prec = c->p.precision;
+    return c->p.lattice == LBCG_D3Q19 && c->p.collision == LBCG_REG &&
+           (prec == LBCG_FP32 || prec == LBCG_FP32_DEV) && c->dims[0] % 4 == 0 &&
+           (c->block_rows == 6 || c->block_rows == 8) && small_index(c) && c->d_status != nullptr &&
+           tma_encoder() != nullptr;
+}
+
+// Tensor map of state buffer `buf` as a 5D float tensor (x, y, z, direction, red/second
+// array) with boxes of kTmaBoxX x wy x 1 x 1 x 2; two cached (the context's two buffers)
+static cudaError_t tma_map_for(lbcg_ctx* c, const void* buf, int wy, const CUtensorMap** out)
+{
+    for (int k = 0; k < 2; ++k)
+        if (c->tmap_buf[k] == buf && c->tmap_wy[k] == wy) {
+            *out = reinterpret_cast<const CUtensorMap*>(c->tmap[k]);
+            return cudaSuccess;
+        }
+    const void* other = buf == c->A ? c->B : c->A;
+    const int k = (c->tmap_buf[0] == other && c->tmap_wy[0] == wy) ? 1 : 0;
+    const cuuint64_t dim[5] = {(cuuint64_t)c->dims[0], (cuuint64_t)c->dims[1], (cuuint64_t)c->dims[2],
+                               (cuuint64_t)c->Q, 2};
+    const cuuint64_t stride[4] = {(cuuint64_t)c->dims[0] * 4, (cuuint64_t)c->dims[0] * c->dims[1] * 4,
+                                  (cuuint64_t)c->np * 4, (cuuint64_t)c->Q * c->np * 4};
+    const cuuint32_t box[5] = {(cuuint32_t)kTmaBoxX, (cuuint32_t)wy, 1, 1, 2};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUtensorMap* m = reinterpret_cast<CUtensorMap*>(c->tmap[k]);
+    const CUresult r = tma_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(buf), dim, stride, box,
+                                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        c->tmap_buf[k] = nullptr;
+        return cudaErrorInvalidValue;
+    }
+    c->tmap_buf[k] = buf;
+    c->tmap_wy[k] = wy;
+    *out = m;
+    return cudaSuccess;
+}
+
+template <int PREC>
+static cudaError_t launch_d3q19_tma(lbcg_ctx* c, const void* a, void* b)
+{
+    using S = typename Store<PREC>::S;
+    const KParams& P = c->kp;
+    const int wy = c->block_rows;
+    const CUtensorMap* m = nullptr;
+    cudaError_t e = tma_map_for(c, a, wy, &m);
+    if (e != cudaSuccess) return e;
+    const int* tl = c->d_tiles;
+    const dim3 grid = tl ? dim3((unsigned)P.ntiles) : dim3(P.nsx, P.nsy, P.nsz);
+    const uint32_t* lk = c->any_link ? c->d_link : nullptr;
+    auto go = [&](auto kern, int bytes, int rows) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        kern<<<grid, dim3(32, rows), (size_t)bytes, c->stream>>>(P, *m, (const S*)a, (S*)b, lk, tl, c->d_status);
+    };
+    if (wy == 8)
+        go(k_step_d3q19_tma<PREC, 8>, TmaLayout<8>::BYTES, 8);
+    else
+        go(k_step_d3q19_tma<PREC, 6>, TmaLayout<6>::BYTES, 6);
+    return cudaGetLastError();
+}
+
 template <int PREC, bool KEEP>
 static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant)
 {
@@ -1190,14 +1565,14 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant
     }
     if (variant == 7 && !KEEP) {
         const size_t smem7 = smem + 2 * 11 * (size_t)wy * 32 * sizeof(T);
-        if (small_index(c)) {
-            cudaFuncSetAttribute(k_step_d3q19_moms<PREC, int>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem7);
-            k_step_d3q19_moms<PREC, int><<<grid, block, smem7, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
-        } else {
-            cudaFuncSetAttribute(k_step_d3q19_moms<PREC, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem7);
-            k_step_d3q19_moms<PREC, long long><<<grid, block, smem7, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
-        }
+        auto go = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem7);
+            kern<<<grid, block, smem7, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+        };
+        if (small_index(c))
+            go(k_step_d3q19_moms<PREC, int>);
+        else
+            go(k_step_d3q19_moms<PREC, long long>);
         return cudaGetLastError();
     }
     if (variant == 6 && !KEEP) {
@@ -1242,6 +1617,7 @@ int effective_variant(const lbcg_ctx* c)
     // populations and re-reads them (three blocks per SM, FP64 two)
     const bool reg = c->p.collision == LBCG_REG;
     int v = c->variant != 0 ? c->variant : (reg ? (prec == LBCG_FP64 ? 6 : 7) : (prec == LBCG_FP64 ? 2 : 5));
+    if (v == 8 && !tma_supported(c)) v = prec == LBCG_FP64 ? 6 : 7;
     if ((v == 6 || v == 7) && !reg) v = prec == LBCG_FP64 ? 2 : 5;
     if (v == 4 && prec != LBCG_FP32 && prec != LBCG_FP32_DEV) v = 2;
     return v;
@@ -1261,6 +1637,10 @@ cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b)
         // default: 5 (re-read, three blocks per SM; measured fastest) for 4- and 2-byte storage;
         // FP64 re-reads with two blocks per SM (it spills at the three-block register budget)
         const int v = effective_variant(c);
+        if (v == 8) {
+            if (prec == LBCG_FP32) return launch_d3q19_tma<LBCG_FP32>(c, a, b);
+            return launch_d3q19_tma<LBCG_FP32_DEV>(c, a, b);
+        }
         const bool keep = v == 1;
         switch (prec) {
             case LBCG_FP64:

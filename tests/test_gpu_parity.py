@@ -120,7 +120,7 @@ def test_fp64_d3q19_step_emulsifier():
 # are held to rounding level.
 @pytest.mark.parametrize("rows,block_rows,variant", [(1, 3, 0), (5, 7, 0), (64, 8, 0), (5, 7, 1), (64, 8, 2), (3, 4, 4), (8, 8, 4),
                                                      (3, 5, 3), (8, 8, 3), (8, 8, 5), (3, 6, 5), (8, 8, 6), (3, 5, 6),
-                                                     (8, 8, 7), (5, 4, 7)])
+                                                     (8, 8, 7), (5, 4, 7), (8, 8, 8), (3, 6, 8)])
 def test_launch_shape_does_not_change_results(rows, block_rows, variant):
     lb = _lb()
     pb = W.step_emulsifier(nx=50, ny=30, nz=10, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10)
@@ -136,6 +136,54 @@ def test_launch_shape_does_not_change_results(rows, block_rows, variant):
                 assert d == 0.0, (prob.name, prec, d)
             else:
                 assert d <= tol, (prob.name, prec, d)
+
+
+# The TMA-staged moment march (variant 8) pulls through shared-memory boxes but computes
+# exactly what the register-pulling moment march (variant 7) computes: identical bits on
+# walled, ported and periodic boxes (periodic edges take the global-load path).
+@pytest.mark.parametrize("block_rows,rows", [(8, 4), (6, 3), (8, 16)])
+def test_tma_staged_march_equals_moment_march(block_rows, rows):
+    lb = _lb()
+    probs = [W.step_emulsifier(nx=64, ny=30, nz=10, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10),
+             W.static_droplet(W.D3Q19, 32, 8, centre=(15.5, 15.5, 15.5)),
+             W.static_droplet(W.D3Q19, 40, 9, ny=20, nz=18, centre=(19.5, 9.5, 8.5))]
+    for prob in probs:
+        for prec in (lb.LBCG_FP32_DEV, lb.LBCG_FP32):
+            a = lb.Simulation(prob, prec, rows=rows, block_rows=block_rows, variant=7)
+            b = lb.Simulation(prob, prec, rows=rows, block_rows=block_rows, variant=8)
+            assert b.launch["variant"] == 8, b.launch
+            a.step(40)
+            b.step(40)
+            assert np.array_equal(a.populations(), b.populations()), (prob.name, prec)
+
+
+def test_tma_unsupported_shape_runs_moment_march():
+    lb = _lb()
+    prob = W.step_emulsifier(nx=50, ny=30, nz=10, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10)  # nx % 4 != 0
+    s = lb.Simulation(prob, lb.LBCG_FP32_DEV, variant=8)
+    assert s.launch["variant"] == 7
+    s64 = lb.Simulation(W.static_droplet(W.D3Q19, 32, 8), lb.LBCG_FP64, variant=8)
+    assert s64.launch["variant"] == 6
+
+
+# Failure path of the bounded pipeline waits: with LBCG_TEST_PIPELINE_STALL=1 at context
+# creation every wait runs out (a phase that expects bytes nobody sends); the kernel records
+# it and returns, the host reports it, and the GPU context stays usable.
+def test_tma_pipeline_timeout_is_reported(monkeypatch):
+    lb = _lb()
+    prob = W.static_droplet(W.D3Q19, 32, 8, centre=(15.5, 15.5, 15.5))
+    monkeypatch.setenv("LBCG_TEST_PIPELINE_STALL", "1")
+    bad = lb.Simulation(prob, lb.LBCG_FP32_DEV, variant=8)
+    monkeypatch.delenv("LBCG_TEST_PIPELINE_STALL")
+    bad.step(1)
+    with pytest.raises(lb.LbcgError, match="timed out"):
+        bad.synchronize()
+    bad.synchronize()  # reported once
+    good = lb.Simulation(prob, lb.LBCG_FP32_DEV, variant=8)
+    ref = lb.Simulation(prob, lb.LBCG_FP32_DEV, variant=7)
+    good.step(10)
+    ref.step(10)
+    assert np.array_equal(good.populations(), ref.populations())
 
 
 def test_deterministic_repeat():
