@@ -112,7 +112,8 @@ def c2(steps: int = 100000, sample: int = 500, A: float = 0.05, u: float = 0.005
     return {"config": "C2 flow focuser D2Q9 1024x192 FP32-dev", "steps": steps, "A": A, "u_max": u,
             "u_max_continuous": u_cont, "flow_rate_ratio_QB_over_QY": u / (2 * u_cont),
             "thread_reach_x_mean": float(np.mean(thread)) if thread else None,
-            "tau_disp": tau_disp, "tau_cont": pb.tau_b, "Ca_estimate": (pb.tau_b - 0.5) / 3 * (2 * u / 3) / (2 * A * pb.tau_b / 9),
+            "tau_disp": tau_disp, "tau_cont": pb.tau_b,
+            "Ca_estimate": (pb.tau_b - 0.5) / 3 * (2 * u_cont / 3) / (2 * A * pb.tau_b / 9),
             "mean_detached_droplets": float(np.mean(counts)) if counts else 0.0,
             "droplets_passing_x768": pinch, "d_over_h_mean": float(np.mean(diam)) if diam else None,
             "d_over_h_std": float(np.std(diam)) if diam else None, "nonfinite": o["nonfinite"], "seconds": dt}
@@ -156,8 +157,12 @@ def main(argv=None):
             res["c2"] = c2(args.c2_steps)
         elif name == "c2scan":
             res["c2scan"] = []
-            for A, ud, uc, td in ((0.1, 0.002, 0.005, 2.0), (0.2, 0.002, 0.005, 2.0), (0.05, 0.001, 0.004, 2.0),
-                                  (0.1, 0.004, 0.01, 2.0), (0.2, 0.001, 0.006, 2.0), (0.3, 0.002, 0.008, 2.0)):
+            # (A, u_max dispersed, u_max continuous, tau dispersed): Ca 0.005-0.05 at the
+            # continuous inlet speed, viscosity ratio 1 to 5
+            for A, ud, uc, td in ((0.1, 0.002, 0.005, 2.0), (0.1, 0.004, 0.01, 2.0), (0.05, 0.005, 0.01, 2.0),
+                                  (0.02, 0.005, 0.01, 2.0), (0.05, 0.01, 0.01, 2.0), (0.02, 0.01, 0.01, 2.0),
+                                  (0.01, 0.005, 0.01, 2.0), (0.05, 0.005, 0.01, 5.0), (0.02, 0.005, 0.01, 1.0),
+                                  (0.02, 0.003, 0.01, 3.0)):
                 r = c2(args.c2_steps, A=A, u=ud, tau_disp=td, u_cont=uc)
                 res["c2scan"].append(r)
                 print(json.dumps(r), flush=True)
