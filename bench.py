@@ -50,10 +50,11 @@ def make_workload(name: str):
         raise SystemExit(str(e))
 
 
-def recorded_traffic(workload: str, precision: str, launch: dict):
-    """DRAM bytes (read + write) per launch of the step kernel, from an ncu record committed
-    under profiles/ for this workload, precision and launch shape, when the step-kernel
-    sources are unchanged since (their digest is part of the record); else None."""
+def recorded(kind: str, workload: str, precision: str, launch: dict):
+    """A per-launch ncu figure of the step kernel (kind "traffic": DRAM bytes read + written;
+    kind "flops": executed FP64 / FP32 flops) from the records committed under profiles/
+    for this workload, precision and launch shape, when the step-kernel sources are
+    unchanged since (their digest is part of the record); else None."""
     from paper_1711_02003_gb300 import build as B
     digest = B.step_kernel_digest()
     want = {"workload": workload, "precision": precision, "variant": str(launch["variant"]),
@@ -67,12 +68,26 @@ def recorded_traffic(workload: str, precision: str, launch: dict):
         with open(os.path.join(pdir, name)) as f:
             for line in f:
                 line = line.strip().strip("`")
-                if not line.startswith("traffic-record:"):
+                if not line.startswith(kind + "-record:"):
                     continue
                 kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
                 if all(kv.get(k) == v for k, v in want.items()):
-                    return int(kv["dram_bytes"]), digest
+                    return kv, digest
     return None, digest
+
+
+def roofline_alu(alu: dict, traffic, k_avg_s: float, hbm_achieved: float, hbm_peak: float, bytes_per_site: int,
+                 fluid: int, digest: str) -> dict:
+    """FP64 runs are bound by the FP64 rate: the roofline is the ALU one (TFLOP/s), with the
+    HBM figures beside it."""
+    ach = None if alu["achieved_gflops"] is None else alu["achieved_gflops"] / 1e3
+    return {"bound": "alu", "achieved": ach, "peak": alu["fma_peak_gflops"] / 1e3, "unit": "TFLOP/s",
+            "frac": alu["frac"], "traffic": traffic, "kernel": "fused step (FP64)",
+            "flops_per_launch": alu["flops_per_launch"], "kernel_ms_avg": k_avg_s * 1e3,
+            "peak_source": "lbcg_fma_peak (FP64 FMA chains, measured in this run)",
+            "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
+                    "bytes_per_site": bytes_per_site, "algorithmic_bytes": bytes_per_site * fluid},
+            "kernel_digest": digest}
 
 
 def peaks():
@@ -181,6 +196,30 @@ def cpu_oracle_sample(pb, budget_s: float = 12.0):
     return rec, s
 
 
+def cpu_suite() -> dict:
+    """The FP64 oracle timed on the host cores, single-threaded and over all threads (the
+    results are bit-identical across thread counts): C1 in full, the C3 box at R = 16 for a
+    bounded number of steps."""
+    import platform
+
+    import oracle
+    allt = oracle.threads()
+    cases = [("C1 static droplet D2Q9 64x64 R=16", W.static_droplet(W.D2Q9, 64, 16), 2000, 2000),
+             ("C3 static droplet D3Q19 128^3 R=16", W.static_droplet(W.D3Q19, 128, 16), 50, 4)]
+    rows = []
+    for name, pb, n_all, n_one in cases:
+        for nt, n in ((allt, n_all), (1, n_one)):
+            oracle.set_threads(nt)
+            sim = oracle.Sim(pb)
+            t0 = time.perf_counter()
+            sim.step(n)
+            dt = time.perf_counter() - t0
+            rows.append({"workload": name, "threads": nt, "steps": n, "seconds": dt,
+                         "MLUPS": pb.fluid_sites() * n / dt / 1e6})
+    oracle.set_threads(allt)
+    return {"cpu_suite": rows, "host": {"machine": platform.machine(), "cpus": os.cpu_count()}, "kind": "oracle"}
+
+
 def error_vs_oracle(sim, osim) -> dict:
     """Max-norm relative error of the GPU fields against the FP64 oracle after the same steps."""
     gr, gb, gu = sim.fields()
@@ -251,6 +290,8 @@ def main():
     ap.add_argument("--workload", default="step_emulsifier")
     ap.add_argument("--precision", default="f32dev", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-suite", action="store_true",
+                    help="only time the FP64 oracle on C1 / C3 (1 and all host threads) and print that line")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-autotune", action="store_true", help="library default launch shape")
     ap.add_argument("--serving-requests", type=int, default=64, help="0 disables the serving sample")
@@ -263,6 +304,10 @@ def main():
                                                                     int(os.environ.get("RANK", "0")), 0)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.cpu_suite:
+        if rank == 0:
+            print(json.dumps(cpu_suite()), flush=True)
         return
 
     import torch
@@ -321,7 +366,21 @@ def main():
     achieved = bytes_per_site * fluid / k_avg_s / 1e9
     peak, peak_kind = peaks()
     eff_launch = sim.launch
-    traffic, digest = recorded_traffic(args.workload, args.precision, eff_launch)
+    rec_t, digest = recorded("traffic", args.workload, args.precision, eff_launch)
+    traffic = int(rec_t["dram_bytes"]) if rec_t else None
+    rec_f, _ = recorded("flops", args.workload, args.precision, eff_launch)
+    # FMA rate of the compute precision on this device (untimed with respect to the run)
+    fma_gflops = lbcg.fma_peak(0 if args.precision == "f64" else 1, stream)
+    flops_launch = None
+    if rec_f:
+        flops_launch = int(rec_f["fp64_flops"] if args.precision == "f64" else rec_f["fp32_flops"])
+    alu = {"fma_peak_gflops": fma_gflops, "precision": "fp64" if args.precision == "f64" else "fp32",
+           "flops_per_launch": flops_launch,
+           "flops_per_fluid_site": None if flops_launch is None else flops_launch / fluid,
+           "achieved_gflops": None if flops_launch is None else flops_launch / k_avg_s / 1e9,
+           "frac": None if flops_launch is None else flops_launch / k_avg_s / 1e9 / fma_gflops,
+           "source": "executed flops (2 FMA + ADD + MUL, ncu record in profiles/, psi-ring recomputation "
+                     "included) / kernel time; peak = lbcg_fma_peak measured now"}
 
     # ---------------------------------------------------------------- end to end through host buffers
     n = pb.nsites
@@ -377,12 +436,15 @@ def main():
                    "launch": dict(eff_launch, tuned=tuned is not None,
                                   tuned_ms=None if tuned is None else tuned["ms"],
                                   candidates=None if tuned is None else len(tuned["table"]))},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "roofline": roofline_alu(alu, traffic, k_avg_s, achieved, peak, bytes_per_site, fluid, digest)
+        if args.precision == "f64" else
+                    {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "traffic_source": "ncu record in profiles/ (dram__bytes_read.sum + "
                      "dram__bytes_write.sum, one launch)" if traffic else "no ncu record for this kernel source and "
                      "launch shape", "algorithmic_bytes": bytes_per_site * fluid, "kernel_digest": digest,
                      "kernel": "fused step", "bytes_per_site": bytes_per_site,
                      "kernel_ms_avg": k_avg_s * 1e3, "peak_source": peak_kind},
+        "alu": alu,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps, "h2d_bytes_total": h2d, "d2h_bytes_total": d2h,
                 "note": "one job: upload initial densities, K steps with observables every 100, read back fields"},

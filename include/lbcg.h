@@ -272,6 +272,13 @@ long long lbcg_batch_remaining(const lbcg_batch* batch, int slot);
 int lbcg_batch_step(lbcg_batch* batch, long long max_steps);
 /* Wait for the batch's work, then report (once each) the slots that have no steps left. */
 int lbcg_batch_poll(lbcg_batch* batch, int* done_slots, int cap, int* ndone);
+/* Multiply-add throughput of the current device in GFLOP/s (2 flops per FMA), measured by
+ * a kernel of independent FMA chains timed with CUDA events on `stream` (synchronises):
+ * precision LBCG_FP64 for FP64, anything else for FP32.  The ALU roofline of the FP64 step
+ * (bound by the FP64 rate, not by HBM) and of the FP32 arithmetic.  Not part of the
+ * method; the paper has no counterpart. */
+int lbcg_fma_peak(int precision, void* stream, double* gflops);
+
 /* Message of the calling thread's last failed batch call. */
 const char* lbcg_batch_last_error(void);
 

@@ -12,7 +12,7 @@ Candidates:
          variant; regularized collision {7, 6 moment march (shared-memory / register
          moments), 5 re-read}, plus 12 and 16 warps per block for variant 7 and the
          TMA-staged march (variant 8; 6 or 8 warps, 8 or 16 planes) for 4-byte storage; BGK
-         {5, 1, 2, 4 (4-byte storage only)}; FP64 regularized {6, 2}, BGK {2, 1}
+         {5, 1, 2, 4 (4-byte storage only)}; FP64 regularized {6, 7, 2}, BGK {2, 1}
 
 Run as a program it prints the candidate table of one named workload, in launch order
 (each candidate: `warm` untimed then `steps` timed launches of its step kernel):
@@ -35,7 +35,7 @@ def candidates(lattice: int, precision: int, collision: int = 0) -> list:
         return [dict(rows=r, block_rows=0, variant=v) for v, r in itertools.product((0, 3), (8, 16, 32, 64))]
     f64 = precision == lbcg.LBCG_FP64
     if collision == 0:  # regularized
-        variants = [6, 2] if f64 else [7, 6, 5]
+        variants = [6, 7, 2] if f64 else [7, 6, 5]
     else:
         variants = [2, 1] if f64 else [5, 1, 2] + ([4] if lbcg.ELEM_BYTES[precision] == 4 else [])
     out = [dict(rows=r, block_rows=b, variant=v) for v, b, r in itertools.product(variants, (4, 6, 8), (4, 8, 16))]

@@ -244,6 +244,13 @@ const char* lbcg_last_error(void) { return g_err.c_str(); }
 
 int lbcg_abi_version(void) { return LBCG_ABI_VERSION; }
 
+int lbcg_fma_peak(int precision, void* stream, double* gflops)
+{
+    std::string err;
+    const int st = lbcg::fma_peak(precision, stream, gflops, err);
+    return st ? fail(st, err) : LBCG_OK;
+}
+
 size_t lbcg_state_bytes(const lbcg_params* p)
 {
     if (validate(p) != LBCG_OK) return 0;

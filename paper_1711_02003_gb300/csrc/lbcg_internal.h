@@ -175,5 +175,7 @@ int build_tiles(lbcg_ctx* c);
 int noalloc_observables(const lbcg_params* p, const void* state, const uint8_t* mask, const double centre[3],
                         double r_in, double r_out, void* stream, lbcg_obs* out, std::string& err);
 size_t storage_size(int precision);
+// peak.cu
+int fma_peak(int precision, void* stream, double* gflops, std::string& err);
 
 }  // namespace lbcg

@@ -612,8 +612,9 @@ __device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename 
     }
 }
 
+// variant 6: moments in registers; three blocks per SM (FP64: two, at 128 registers)
 template <int PREC, typename IDX>
-__global__ void __launch_bounds__(256, 3) k_step_d3q19_mom(const KParams P,
+__global__ void __launch_bounds__(256, PREC == LBCG_FP64 ? 2 : 3) k_step_d3q19_mom(const KParams P,
                                                            const typename Store<PREC>::S* __restrict__ A,
                                                            typename Store<PREC>::S* __restrict__ B,
                                                            const uint32_t* __restrict__ link, const int* __restrict__ tiles)

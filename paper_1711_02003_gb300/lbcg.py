@@ -88,6 +88,7 @@ _PROTOS = {
     "lbcg_kernel_time": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong)]),
     "lbcg_set_launch": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
     "lbcg_get_launch": (C.c_int, [_vp, _ip, _ip, _ip]),
+    "lbcg_fma_peak": (C.c_int, [C.c_int, _vp, _dp]),
     "lbcg_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp)]),
     "lbcg_batch_destroy": (None, [_vp]),
     "lbcg_batch_add": (C.c_int, [_vp, _vp, C.c_longlong, C.POINTER(C.c_int)]),
@@ -142,6 +143,15 @@ def ports_of(pb):
         arr[m].normal_sign, arr[m].profile = int(pt.normal_sign), int(pt.profile)
         arr[m].u_max, arr[m].rho, arr[m].psi = float(pt.u_max), float(pt.rho), float(pt.psi)
     return arr
+
+
+def fma_peak(precision: int = 0, stream=None) -> float:
+    """Measured multiply-add throughput of the current device, GFLOP/s (FP64 or FP32)."""
+    load()
+    g = C.c_double()
+    sp = C.c_void_p(stream.cuda_stream if stream is not None else 0)
+    _check("lbcg_fma_peak", _lib.lbcg_fma_peak(int(precision), sp, C.byref(g)))
+    return g.value
 
 
 def state_bytes(pb, precision: int) -> int:

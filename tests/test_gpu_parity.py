@@ -354,3 +354,11 @@ def test_full_size_step_emulsifier_fp32dev():
     g.step(20)
     b = g.observables((384, 64, 16))
     assert abs(b["mass_r"] / a["mass_r"] - 1) < 1e-5 and abs(b["mass_b"] / a["mass_b"] - 1) < 1e-5
+
+
+def test_fma_peak_measures_both_precisions():
+    lb = _lb()
+    f64 = lb.fma_peak(lb.LBCG_FP64)
+    f32 = lb.fma_peak(lb.LBCG_FP32)
+    assert f64 > 0 and f32 > 0
+    assert f32 > 4 * f64  # GB300's FP64 rate is a small fraction of its FP32 rate
