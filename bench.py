@@ -297,6 +297,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=64, help="0 disables the serving sample")
     ap.add_argument("--serving-steps-scale", type=float, default=0.25)
     ap.add_argument("--serving-baseline", type=int, default=6)
+    ap.add_argument("--serving-only", action="store_true",
+                    help="only run the serving workload (--serving-requests, --serving-steps-scale) and print it")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -308,6 +310,16 @@ def main():
     if args.cpu_suite:
         if rank == 0:
             print(json.dumps(cpu_suite()), flush=True)
+        return
+    if args.serving_only:
+        if rank == 0:
+            import torch
+            from paper_1711_02003_gb300 import lbcg
+            lbcg.load()
+            torch.cuda.set_device(local)
+            t0 = time.perf_counter()
+            out = serving_sample(args.serving_requests, args.serving_steps_scale, args.serving_baseline)
+            print(json.dumps({"serving": out, "wall_s": time.perf_counter() - t0}), flush=True)
         return
 
     import torch
