@@ -231,15 +231,17 @@ def error_vs_oracle(sim, osim) -> dict:
             "u_abs": float(np.abs(gu - ou).max())}
 
 
-def serving_sample(n_requests: int, steps_scale: float, baseline_n: int, rate: float = 20.0) -> dict:
+def serving_sample(n_requests: int, steps_scale: float, baseline_n: int, rate: float = 20.0,
+                   slots: int = 64) -> dict:
     """Continuous-batching serving of the mixed request workload (FP32-dev batches under a
     150 GB HBM budget) and the one-at-a-time FP64 baseline on the first requests."""
     from paper_1711_02003_gb300 import serve
     reqs = serve.make_requests(n_requests, rate=rate, seed=0, steps_scale=steps_scale)
-    eng = serve.LbcgEngine(precision=PREC["f32dev"], max_slots=64)
+    eng = serve.LbcgEngine(precision=PREC["f32dev"], max_slots=slots)
     srv = serve.Server(eng, hbm_budget=150e9, chunk=100)
     res = srv.run(reqs, realtime=True)
     out = {"requests": n_requests, "arrival_rate_per_s": rate, "steps_scale": steps_scale, "hbm_budget_gb": 150,
+           "slots_per_lattice": slots,
            "precision": "f32dev", "peak_resident": srv.peak_resident, "peak_hbm_gb": srv.peak_used / 1e9}
     out.update({k: v for k, v in serve.summary(res).items()})
     if baseline_n:
@@ -297,6 +299,7 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=64, help="0 disables the serving sample")
     ap.add_argument("--serving-steps-scale", type=float, default=0.25)
     ap.add_argument("--serving-baseline", type=int, default=6)
+    ap.add_argument("--serving-slots", type=int, default=64, help="batch slots per lattice")
     ap.add_argument("--serving-only", action="store_true",
                     help="only run the serving workload (--serving-requests, --serving-steps-scale) and print it")
     args = ap.parse_args()
@@ -318,7 +321,8 @@ def main():
             lbcg.load()
             torch.cuda.set_device(local)
             t0 = time.perf_counter()
-            out = serving_sample(args.serving_requests, args.serving_steps_scale, args.serving_baseline)
+            out = serving_sample(args.serving_requests, args.serving_steps_scale, args.serving_baseline,
+                                 slots=args.serving_slots)
             print(json.dumps({"serving": out, "wall_s": time.perf_counter() - t0}), flush=True)
         return
 

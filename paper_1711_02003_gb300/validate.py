@@ -1,6 +1,6 @@
 """Validation runs of the configurations on the GPU (physics and precision checks).
 
-    python -m paper_1711_02003_gb300.validate [--only c1,c3,c2,f1] [--out results.json]
+    python -m paper_1711_02003_gb300.validate [--only c1,c3,c2,f1,f2,c2scan,c2drip] [--out results.json]
 
 c1  static droplet D2Q9 64^2, R = 16, FP64, 2000 steps: per-component mass drift and the Laplace
     pressure against sigma/R with sigma = 2 A tau / 9 (parity with the oracle is in the tests).
@@ -12,6 +12,12 @@ c2  flow-focusing cross junction D2Q9 1024 x 192, FP32-dev, 1e5 steps: droplets 
     count, pinch-offs counted as new droplets passing x = 768, and equivalent diameters d/h.
 f1  regularized vs BGK relaxation for a resting droplet with relaxation times 1 (continuous) and
     5 (droplet), as in Fig. 1: max |u| ratio, 2D and 3D.
+f2  density ratio 1, 2, 5, 10 through alpha_k (D2Q9 128^2 R = 24, D3Q19 96^3 R = 16, 5000 steps):
+    Laplace law against the unit-ratio sigma, spurious currents, mass drift, FP32-dev vs FP64.
+c2scan / c2drip  flow-focuser regime scans (pinch-off counts, d/h) over A, inlet speeds and
+    viscosity ratio.
+f3  d/h against Q_B / (2 Q_Y) in the flow focuser (2e5 steps per case) and its fitted exponent
+    (the paper reports 0.5, after Cubaud and Mason).
 """
 from __future__ import annotations
 
@@ -110,7 +116,7 @@ def c2(steps: int = 100000, sample: int = 500, A: float = 0.05, u: float = 0.005
     dt = time.perf_counter() - t0
     o = sim.observables((nx / 2, pb.ny / 2), allow_diverged=True)
     return {"config": "C2 flow focuser D2Q9 1024x192 FP32-dev", "steps": steps, "A": A, "u_max": u,
-            "u_max_continuous": u_cont, "flow_rate_ratio_QB_over_QY": u / (2 * u_cont),
+            "u_max_continuous": u_cont, "q_b_over_2q_y": u / (2 * u_cont),
             "thread_reach_x_mean": float(np.mean(thread)) if thread else None,
             "tau_disp": tau_disp, "tau_cont": pb.tau_b,
             "Ca_estimate": (pb.tau_b - 0.5) / 3 * (2 * u_cont / 3) / (2 * A * pb.tau_b / 9),
@@ -135,6 +141,56 @@ def f1() -> list:
                "bgk_over_reg": umax[W.BGK] / umax[W.REG]}
         out.append(rec)
         print(json.dumps(rec), flush=True)
+    return out
+
+
+def f2(steps: int = 5000) -> list:
+    """Density ratio through alpha_k (Eqs. 7-8): resting droplets holding gamma times the
+    surrounding density, Laplace law against the unit-ratio sigma, spurious currents, mass
+    drift; FP32-dev against FP64."""
+    rows = []
+    for lat, n, R, centre in ((W.D2Q9, 128, 24, None), (W.D3Q19, 96, 16, (47.5, 47.5, 47.5))):
+        for g in (1.0, 2.0, 5.0, 10.0):
+            pb = W.static_droplet(lat, n, R, centre=centre, density_ratio=g)
+            sigma = 2 * pb.A * pb.tau_r / 9
+            c = centre or (n // 2, n // 2, n // 2)
+            rec = {"config": f"f2 {'D2Q9' if lat == W.D2Q9 else 'D3Q19'} {n} R={R}", "density_ratio": g,
+                   "alpha_r": pb.alpha_r, "alpha_b": pb.alpha_b, "steps": steps}
+            for prec in (lbcg.LBCG_FP32_DEV, lbcg.LBCG_FP64):
+                sim = lbcg.Simulation(pb, prec)
+                o0 = sim.observables(c, allow_diverged=True)
+                sim.step(steps)
+                o = sim.observables(c, allow_diverged=True)
+                k = 1 if lat == W.D2Q9 else 2
+                rec[lbcg.PRECISION_NAMES[prec]] = {
+                    "dp": o["dp"], "r_eff": o["r_eff"], "dp_r_over_k_sigma": o["dp"] * o["r_eff"] / (k * sigma),
+                    "umax": o["umax"], "mass_drift_r": o["mass_r"] / o0["mass_r"] - 1,
+                    "mass_drift_b": o["mass_b"] / o0["mass_b"] - 1, "nonfinite": o["nonfinite"]}
+                sim.close()
+            rec["f32dev_vs_f64_dp_rel"] = rec["f32dev"]["dp"] / rec["f64"]["dp"] - 1
+            rows.append(rec)
+            print(json.dumps(rec), flush=True)
+    return rows
+
+
+def f3(steps: int = 200000) -> dict:
+    """Droplet size against the flow-rate ratio in the flow focuser (Sec. IV A): continuous
+    inlets at u_max 0.01, dispersed inlet swept, Ca 0.05 and 0.025 (A 0.1, 0.2), viscosity
+    ratio 2; least-squares exponent of d/h against Q_B / (2 Q_Y) over the cases that pinch off."""
+    out = {"cases": [], "fits": {}}
+    for A in (0.1, 0.2):
+        xs, ys = [], []
+        for ud in (0.003, 0.004, 0.005, 0.006, 0.008):
+            r = c2(steps, A=A, u=ud, tau_disp=2.0, u_cont=0.01)
+            out["cases"].append(r)
+            print(json.dumps(r), flush=True)
+            if r["droplets_passing_x768"] >= 2 and r["d_over_h_mean"]:
+                xs.append(math.log(r["q_b_over_2q_y"]))
+                ys.append(math.log(r["d_over_h_mean"]))
+        if len(xs) >= 2:
+            k, c = np.polyfit(xs, ys, 1)
+            out["fits"][f"A={A}"] = {"exponent": float(k), "prefactor": float(math.exp(c)), "points": len(xs)}
+    print(json.dumps(out["fits"]), flush=True)
     return out
 
 
@@ -168,6 +224,19 @@ def main(argv=None):
                 print(json.dumps(r), flush=True)
         elif name == "f1":
             res["f1"] = f1()
+        elif name == "f2":
+            res["f2"] = f2()
+        elif name == "f3":
+            res["f3"] = f3(2 * args.c2_steps)
+        elif name == "c2drip":
+            # dripping-regime search: continuous inlet 0.01 (Ca 0.025-0.05 via A), slower
+            # dispersed inlets, viscosity ratio 1-3; 2e5 steps
+            res["c2drip"] = []
+            for A, ud, td in ((0.1, 0.002, 1.0), (0.1, 0.003, 2.0), (0.1, 0.004, 1.0), (0.2, 0.002, 2.0),
+                              (0.2, 0.004, 2.0), (0.2, 0.006, 2.0), (0.1, 0.006, 3.0), (0.15, 0.004, 3.0)):
+                r = c2(2 * args.c2_steps, A=A, u=ud, tau_disp=td, u_cont=0.01)
+                res["c2drip"].append(r)
+                print(json.dumps(r), flush=True)
         print(json.dumps({name: res.get(name), "seconds": time.perf_counter() - t0}, default=float), flush=True)
     if args.out:
         with open(args.out, "w") as f:

@@ -140,12 +140,15 @@ def _two_phase_fields(psi: np.ndarray, rho0: float, mask: np.ndarray):
 def static_droplet(lattice: int = D2Q9, n: int = 64, R: float = 16, *, nz: int | None = None,
                    tau_r: float = 1.0, tau_b: float = 1.0, A: float = 0.01, beta: float = 0.7,
                    rho0: float = 1.0, collision: int = REG, ny: int | None = None,
-                   centre=None) -> Problem:
+                   centre=None, density_ratio: float = 1.0) -> Problem:
     """Centred resting droplet in a fully periodic box (Fig. 1 setting).
 
     psi = +1 strictly inside (integer test (x-xc)^2 + (y-yc)^2 [+ (z-zc)^2] < R^2,
     default centre n/2), -1 outside; rho_R = rho0 (1+psi)/2, rho_B = rho0 (1-psi)/2,
-    fluid at rest."""
+    fluid at rest.  density_ratio = gamma != 1: the droplet (red) holds gamma * rho0, the
+    surrounding fluid rho0, and alpha_R = 1 - (1 - alpha_B) / gamma with alpha_B the unit-
+    ratio value, so that the two bulk pressures of Eq. 8 (proportional to rho^k (1 - alpha_k))
+    are equal."""
     nx = n
     ny = n if ny is None else ny
     if lattice == D2Q9:
@@ -161,10 +164,15 @@ def static_droplet(lattice: int = D2Q9, n: int = 64, R: float = 16, *, nz: int |
     mask = np.zeros(nx * ny * nzz, dtype=np.uint8)
     rho_r, rho_b = _two_phase_fields(psi, rho0, mask)
     alpha = ALPHA_UNIT_RATIO[lattice]
+    alpha_r = alpha
+    if density_ratio != 1.0:
+        rho_r = rho_r * density_ratio
+        alpha_r = 1.0 - (1.0 - alpha) / density_ratio
+    tag = "" if density_ratio == 1.0 else f" ratio={density_ratio:g}"
     return Problem(lattice=lattice, nx=nx, ny=ny, nz=nzz, periodic=(1, 1, 1), tau_r=tau_r, tau_b=tau_b,
-                   alpha_r=alpha, alpha_b=alpha, A=A, beta=beta, rho0=rho0, collision=collision,
+                   alpha_r=alpha_r, alpha_b=alpha, A=A, beta=beta, rho0=rho0, collision=collision,
                    mask=mask, ports=[], rho_r=rho_r, rho_b=rho_b, u=None,
-                   name=f"static droplet {'D2Q9' if lattice == D2Q9 else 'D3Q19'} n={n} R={R}")
+                   name=f"static droplet {'D2Q9' if lattice == D2Q9 else 'D3Q19'} n={n} R={R}{tag}")
 
 
 def shear_wave(lattice: int = D2Q9, n: int = 32, U: float = 1e-3, tau: float = 1.0) -> Problem:

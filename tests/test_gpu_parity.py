@@ -80,6 +80,19 @@ def test_fp64_density_ratio_alpha():
     assert np.abs(g.populations() - o.populations()).max() <= 1e-11
 
 
+@pytest.mark.parametrize("ratio", [2.0, 5.0])
+def test_fp64_density_ratio_droplet(ratio):
+    pb = W.static_droplet(W.D2Q9, 40, 9, density_ratio=ratio)
+    g, o = run_pair(pb, 300)
+    assert np.abs(g.populations() - o.populations()).max() <= 1e-11
+
+
+def test_fp64_density_ratio_droplet_3d():
+    pb = W.static_droplet(W.D3Q19, 24, 6.5, ny=20, nz=18, centre=(11.5, 9.5, 8.5), density_ratio=3.0)
+    g, o = run_pair(pb, 150)
+    assert np.abs(g.populations() - o.populations()).max() <= 1e-11
+
+
 def slab(pb):
     """Red slab x in [nx/4, 3nx/4): planar interfaces (for boxes too small for a droplet)."""
     x = np.arange(pb.nsites) % pb.nx

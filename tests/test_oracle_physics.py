@@ -156,6 +156,26 @@ def test_laplace_law_2d():
     assert errs[0] > errs[1] > errs[2]
 
 
+@pytest.mark.parametrize("ratio", [2.0, 5.0])
+def test_laplace_law_density_ratio(ratio):
+    """Density ratio gamma != 1 through alpha_k (Eqs. 7-8): the droplet holds gamma times the
+    surrounding density with alpha_R chosen for equal bulk pressures.  The surface stress of
+    Eq. 9 depends on psi alone (+-1 in both bulks whatever the densities), so the same
+    sigma = 2 A tau / 9 must give Delta p = sigma / R; component masses stay conserved."""
+    A, tau = 0.01, 1.0
+    sigma = 2 * A * tau / 9
+    pb = W.static_droplet(W.D2Q9, 48, 12, A=A, tau_r=tau, tau_b=tau, density_ratio=ratio)
+    assert pb.alpha_r > pb.alpha_b
+    s = oracle.Sim(pb)
+    o0 = s.observables((24, 24))
+    s.step(3000)
+    o = s.observables((24, 24))
+    assert o["dp"] > 0
+    assert abs(o["dp"] * o["r_eff"] / sigma - 1) < 0.06
+    assert abs(o["mass_r"] / o0["mass_r"] - 1) < 1e-12
+    assert abs(o["mass_b"] / o0["mass_b"] - 1) < 1e-12
+
+
 def test_laplace_law_3d():
     A, tau = 0.01, 2.0
     sigma = 2 * A * tau / 9
