@@ -30,7 +30,7 @@ struct lbcg_batch {
     std::vector<long long> remaining;     // steps still to run
     std::vector<char> reported;           // completion already returned by poll
     std::vector<KParams> kp;              // per-slot launch-shaped parameters
-    BatchSlot* h_slots = nullptr;         // pinned
+    BatchSlot* h_slots = nullptr;         // pinned, two tables (replays alternate between them)
     BatchSlot* d_slots = nullptr;
     std::vector<BatchItem> h_items, h_fill;
     BatchItem* d_items = nullptr;
@@ -39,7 +39,8 @@ struct lbcg_batch {
     int items_cap = 0, fill_cap = 0;
     bool dirty = true;                    // membership changed: rebuild work lists
     cudaGraphExec_t graph = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t done[2] = {nullptr, nullptr};  // last replay that read table 0 / 1
+    long long nrep = 0;                   // replays launched
 };
 
 namespace {
@@ -155,15 +156,16 @@ int lbcg_batch_create(int lattice, int precision, int max_instances, void* strea
     b->remaining.assign(max_instances, 0);
     b->reported.assign(max_instances, 0);
     b->kp.resize(max_instances);
-    bool ok = cudaMallocHost(&b->h_slots, sizeof(BatchSlot) * max_instances) == cudaSuccess &&
+    bool ok = cudaMallocHost(&b->h_slots, 2 * sizeof(BatchSlot) * max_instances) == cudaSuccess &&
               cudaMalloc(&b->d_slots, sizeof(BatchSlot) * max_instances) == cudaSuccess &&
               cudaMalloc(&b->d_counts, 2 * sizeof(int)) == cudaSuccess &&
-              cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&b->done[0], cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->done[1], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         lbcg_batch_destroy(b);
         return bfail(LBCG_ERR_NOMEM, "batch tables allocation failed");
     }
-    std::memset(b->h_slots, 0, sizeof(BatchSlot) * max_instances);
+    std::memset(b->h_slots, 0, 2 * sizeof(BatchSlot) * max_instances);
     cudaMemsetAsync(b->d_slots, 0, sizeof(BatchSlot) * max_instances, b->stream);
     cudaMemsetAsync(b->d_counts, 0, 2 * sizeof(int), b->stream);
     *out = b;
@@ -176,7 +178,8 @@ void lbcg_batch_destroy(lbcg_batch* b)
     cudaStreamSynchronize(b->stream);
     drop_graph(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    if (b->done) cudaEventDestroy(b->done);
+    for (cudaEvent_t e : b->done)
+        if (e) cudaEventDestroy(e);
     cudaFreeHost(b->h_slots);
     cudaFree(b->d_slots);
     cudaFree(b->d_items);
@@ -245,12 +248,16 @@ int lbcg_batch_step(lbcg_batch* b, long long max_steps)
         }
         int st = capture(b);
         if (st) return st;
-        // the previous replay must have consumed the pinned slot table before it is rewritten
-        cudaError_t e = cudaEventSynchronize(b->done);
+        // two pinned tables alternate between replays: the replay before the previous one
+        // must have copied this table before it is rewritten (so the host runs ahead by a
+        // replay instead of waiting for the GPU at every one)
+        const int k = (int)(b->nrep & 1);
+        BatchSlot* const tab = b->h_slots + (size_t)k * b->max_slots;
+        cudaError_t e = cudaEventSynchronize(b->done[k]);
         if (e != cudaSuccess) return bfail(LBCG_ERR_CUDA, cudaGetErrorString(e));
         const long long chunk = std::min<long long>(kBatchGraphSteps, max_steps - done);
         for (int s = 0; s < b->max_slots; ++s) {
-            BatchSlot& h = b->h_slots[s];
+            BatchSlot& h = tab[s];
             lbcg_ctx* c = b->ctx[s];
             if (!c) {
                 h.steps = 0;
@@ -265,15 +272,15 @@ int lbcg_batch_step(lbcg_batch* b, long long max_steps)
             h.nghost = c->nghost;
             h.steps = (int)std::min<long long>(chunk, b->remaining[s]);
         }
-        e = cudaMemcpyAsync(b->d_slots, b->h_slots, sizeof(BatchSlot) * b->max_slots, cudaMemcpyHostToDevice,
-                            b->stream);
+        e = cudaMemcpyAsync(b->d_slots, tab, sizeof(BatchSlot) * b->max_slots, cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(b->done, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(b->done[k], b->stream);
+        ++b->nrep;
         if (e != cudaSuccess) return bfail(LBCG_ERR_CUDA, std::string("batch replay: ") + cudaGetErrorString(e));
         for (int s = 0; s < b->max_slots; ++s) {
             lbcg_ctx* c = b->ctx[s];
             if (!c) continue;
-            const int n = b->h_slots[s].steps;
+            const int n = tab[s].steps;
             if (n & 1) std::swap(c->A, c->B);
             c->step += n;
             b->remaining[s] -= n;

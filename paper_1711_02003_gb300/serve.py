@@ -171,8 +171,15 @@ class Server:
         live = {}
         results = []
         while queue or live:
-            t = now()
+            # the resident requests advance asynchronously; the host admits meanwhile, so
+            # instance set-up (allocation, geometry tables, initial state) overlaps GPU work
+            advanced = bool(live)
+            if advanced:
+                self.engine.advance(self.chunk)
+                if not realtime:
+                    vclock += 1e-3
             # admission: arrived, fits the budget, free slot (first come, first served)
+            t = now()
             while queue and queue[0].arrival <= t:
                 r = queue[0]
                 need = self.engine.state_bytes(r)
@@ -191,9 +198,8 @@ class Server:
                     else:
                         vclock = max(vclock, queue[0].arrival)
                 continue
-            self.engine.advance(self.chunk)
-            if not realtime:
-                vclock += 1e-3
+            if not advanced:
+                continue
             for h in self.engine.finished():
                 r, need, t_adm = live.pop(h)
                 obs = self.engine.retire(h)
