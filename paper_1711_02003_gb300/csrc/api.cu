@@ -182,26 +182,71 @@ int build_tiles(lbcg_ctx* c)
     c->kp.ntiles = 0;
     if (!c->geometry || !c->any_link) return LBCG_OK;
     const KParams& k = c->kp;
-    const int nx = c->dims[0], ny = c->dims[1];
-    const long long ntot = (long long)k.nsx * k.nsy * k.nsz;
-    std::vector<char> on((size_t)ntot, 0);
-    const int ty = c->p.lattice == LBCG_D2Q9 ? k.rows : c->block_rows - 2;
-    const int tz = c->p.lattice == LBCG_D2Q9 ? 1 : k.rows;
-    for (long long s = 0; s < c->n; ++s) {
-        if (c->mask[s] != LBCG_MASK_FLUID) continue;
-        const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
-        on[(size_t)((x / 30) + (long long)k.nsx * ((y / ty) + (long long)k.nsy * (z / tz)))] = 1;
-    }
+    const int nx = c->dims[0], ny = c->dims[1], nz = c->dims[2];
     std::vector<int> list;
-    for (long long t = 0; t < ntot; ++t)
-        if (on[(size_t)t]) list.push_back((int)t);
-    if ((long long)list.size() == ntot) return LBCG_OK;  // nothing to skip
-    if (list.empty()) list.push_back(0);
+    if (c->p.lattice == LBCG_D2Q9) {
+        // strips of 30 x rows sites holding a fluid site
+        const long long ntot = (long long)k.nsx * k.nsy;
+        std::vector<char> on((size_t)ntot, 0);
+        for (long long s = 0; s < c->n; ++s) {
+            if (c->mask[s] != LBCG_MASK_FLUID) continue;
+            const int x = (int)(s % nx), y = (int)(s / nx);
+            on[(size_t)((x / 30) + (long long)k.nsx * (y / k.rows))] = 1;
+        }
+        for (long long t = 0; t < ntot; ++t)
+            if (on[(size_t)t]) list.push_back((int)t);
+        if ((long long)list.size() == ntot) return LBCG_OK;  // nothing to skip
+        if (list.empty()) list.push_back(0);
+    } else {
+        // for each x-y column of 30 x (block_rows - 2) sites: the planes holding a fluid site,
+        // grouped in runs of consecutive planes, each run cut into near-equal z-ranges of at
+        // most `rows` planes (a terrace 8 planes high gets two ranges of 4, not a range of 4
+        // and one of 4 holding one fluid plane); entries (column, z0 | z1 << 16) ordered by
+        // range, then column
+        if (nz > 0xffff) return fail(LBCG_ERR_GEOMETRY, "nz above 65535 with walls");
+        const int ty = c->block_rows - 2;
+        const long long ncol = (long long)k.nsx * k.nsy;
+        std::vector<char> has((size_t)(ncol * nz), 0);
+        for (long long s = 0; s < c->n; ++s) {
+            if (c->mask[s] != LBCG_MASK_FLUID) continue;
+            const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
+            has[(size_t)(((x / 30) + (long long)k.nsx * (y / ty)) * nz + z)] = 1;
+        }
+        std::vector<std::vector<std::pair<int, int>>> ranges((size_t)ncol);
+        size_t depth = 0;
+        for (long long col = 0; col < ncol; ++col) {
+            const char* h = &has[(size_t)(col * nz)];
+            for (int z = 0; z < nz;) {
+                if (!h[z]) {
+                    ++z;
+                    continue;
+                }
+                int e = z;
+                while (e < nz && h[e]) ++e;
+                const int len = e - z, parts = (len + k.rows - 1) / k.rows;
+                for (int q = 0; q < parts; ++q)
+                    ranges[(size_t)col].push_back({z + (int)((long long)len * q / parts),
+                                                   z + (int)((long long)len * (q + 1) / parts)});
+                z = e;
+            }
+            depth = std::max(depth, ranges[(size_t)col].size());
+        }
+        for (size_t d = 0; d < depth; ++d)
+            for (long long col = 0; col < ncol; ++col)
+                if (d < ranges[(size_t)col].size()) {
+                    list.push_back((int)col);
+                    list.push_back(ranges[(size_t)col][d].first | (ranges[(size_t)col][d].second << 16));
+                }
+        if (list.empty()) {
+            list.push_back(0);
+            list.push_back(0);  // an empty range: the block pulls ring planes only
+        }
+    }
     if (cudaMalloc(&c->d_tiles, sizeof(int) * list.size()) != cudaSuccess)
         return fail(LBCG_ERR_NOMEM, "tile list allocation failed");
     if (cudaMemcpy(c->d_tiles, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(LBCG_ERR_CUDA, "tile list copy failed");
-    c->ntiles = (int)list.size();
+    c->ntiles = (int)(c->p.lattice == LBCG_D2Q9 ? list.size() : list.size() / 2);
     c->kp.ntiles = c->ntiles;
     return LBCG_OK;
 }

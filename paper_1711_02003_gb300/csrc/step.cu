@@ -156,8 +156,10 @@ __device__ __forceinline__ void store_site(const KParams& P, typename Store<PREC
 }
 
 // Tiles with at least one fluid site, when the geometry has walls: the launch covers only
-// those (P.ntiles entries of `tiles`, each the linear index of a 2D strip or a 3D block
-// tile); without a list every tile of the box is launched.
+// those (P.ntiles entries of `tiles`: D2Q9, the linear index of a strip; D3Q19, two ints
+// per block tile, the linear index of its x-y column and its z-range z0 | z1 << 16, cut to
+// the runs of planes of the column that hold fluid); without a list every tile of the box
+// is launched, the z-range of block z being [z * rows, min(z * rows + rows, nz)).
 __device__ __forceinline__ bool strip_of(const KParams& P, const int* __restrict__ tiles, int gw, int& sxi, int& syi)
 {
     int t = gw;
@@ -172,17 +174,21 @@ __device__ __forceinline__ bool strip_of(const KParams& P, const int* __restrict
     return true;
 }
 
-__device__ __forceinline__ void block_of(const KParams& P, const int* __restrict__ tiles, int& bx, int& by, int& bz)
+__device__ __forceinline__ void block_of(const KParams& P, const int* __restrict__ tiles, int& bx, int& by, int& z0,
+                                         int& z1)
 {
     if (tiles) {
-        const int t = tiles[blockIdx.x];
+        const int t = tiles[2 * blockIdx.x];
+        const int zr = tiles[2 * blockIdx.x + 1];
         bx = t % P.nsx;
-        by = (t / P.nsx) % P.nsy;
-        bz = t / (P.nsx * P.nsy);
+        by = t / P.nsx;
+        z0 = zr & 0xffff;
+        z1 = zr >> 16;
     } else {
         bx = blockIdx.x;
         by = blockIdx.y;
-        bz = blockIdx.z;
+        z0 = (int)blockIdx.z * P.rows;
+        z1 = min(z0 + P.rows, P.nz);
     }
 }
 
@@ -289,12 +295,12 @@ __global__ void __launch_bounds__(256) k_step_d2q9(const KParams P, const typena
 
 // ----------------------------------------------------------------------- D3Q19
 // blockDim = (32, WY); warp w owns row y = by*(WY-2) + w - 1; rows 1..WY-2 collide.
-// one block: the tile (bx, by) of 30 x (WY-2) sites over the z-chunk bz; psi_s holds
+// one block: the tile (bx, by) of 30 x (WY-2) sites over the planes [z0, z1); psi_s holds
 // 4 * WY * 32 values of shared memory
 template <int PREC, bool KEEP, typename IDX>
 __device__ __forceinline__ void tile_d3q19(const KParams& P, const typename Store<PREC>::S* __restrict__ A,
                                            typename Store<PREC>::S* __restrict__ B, const uint32_t* __restrict__ link,
-                                           int bx, int by, int bz, typename Store<PREC>::T* psi_s)
+                                           int bx, int by, int z0, int z1, typename Store<PREC>::T* psi_s)
 {
     using T = typename Store<PREC>::T;
     using L = Lat<1>;
@@ -319,8 +325,6 @@ __device__ __forceinline__ void tile_d3q19(const KParams& P, const typename Stor
         u.yp = (long long)b * nx;
     }
     const IDX sxy = (IDX)xs + (IDX)nx * (IDX)ys;
-    const int z0 = bz * P.rows;
-    const int z1 = min(z0 + P.rows, nz);
     const T psi_wall = phys<T>(P).psi_wall;
 
     T rb[Q], gb[Q];
@@ -405,9 +409,9 @@ __global__ void __launch_bounds__(256, 2) k_step_d3q19(const KParams P,
                                                        const uint32_t* __restrict__ link, const int* __restrict__ tiles)
 {
     extern __shared__ unsigned char smem_raw[];
-    int bx, by, bz;
-    block_of(P, tiles, bx, by, bz);
-    tile_d3q19<PREC, KEEP, IDX>(P, A, B, link, bx, by, bz, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+    int bx, by, z0, z1;
+    block_of(P, tiles, bx, by, z0, z1);
+    tile_d3q19<PREC, KEEP, IDX>(P, A, B, link, bx, by, z0, z1, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
 }
 
 // variant 5: re-read variant compiled for three resident blocks per SM (<= 85 registers)
@@ -418,9 +422,9 @@ __global__ void __launch_bounds__(256, 3) k_step_d3q19_occ(const KParams P,
                                                            const uint32_t* __restrict__ link, const int* __restrict__ tiles)
 {
     extern __shared__ unsigned char smem_raw[];
-    int bx, by, bz;
-    block_of(P, tiles, bx, by, bz);
-    tile_d3q19<PREC, false, IDX>(P, A, B, link, bx, by, bz, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+    int bx, by, z0, z1;
+    block_of(P, tiles, bx, by, z0, z1);
+    tile_d3q19<PREC, false, IDX>(P, A, B, link, bx, by, z0, z1, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
 }
 
 // ------------------------------------------------- moment march (variants 6, 7; regularized)
@@ -510,7 +514,7 @@ __device__ __forceinline__ typename Store<PREC>::T pull_moments(const KParams& P
 template <int PREC, typename IDX, bool MSMEM>
 __device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename Store<PREC>::S* __restrict__ A,
                                                typename Store<PREC>::S* __restrict__ B,
-                                               const uint32_t* __restrict__ link, int bx, int by, int bz,
+                                               const uint32_t* __restrict__ link, int bx, int by, int z0, int z1,
                                                typename Store<PREC>::T* psi_s)
 {
     using T = typename Store<PREC>::T;
@@ -539,8 +543,6 @@ __device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename 
     }
     const IDX sxy = (IDX)xs + (IDX)nx * (IDX)ys;
     const IDX np = (IDX)P.np;
-    const int z0 = bz * P.rows;
-    const int z1 = min(z0 + P.rows, nz);
     const Phys<T>& ph = phys<T>(P);
     const T psi_wall = ph.psi_wall;
 
@@ -620,9 +622,9 @@ __global__ void __launch_bounds__(256, PREC == LBCG_FP64 ? 2 : 3) k_step_d3q19_m
                                                            const uint32_t* __restrict__ link, const int* __restrict__ tiles)
 {
     extern __shared__ unsigned char smem_raw[];
-    int bx, by, bz;
-    block_of(P, tiles, bx, by, bz);
-    tile_d3q19_mom<PREC, IDX, false>(P, A, B, link, bx, by, bz, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+    int bx, by, z0, z1;
+    block_of(P, tiles, bx, by, z0, z1);
+    tile_d3q19_mom<PREC, IDX, false>(P, A, B, link, bx, by, z0, z1, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
 }
 
 // variant 7: the moment march with the waiting moments in shared memory; 64 registers, so
@@ -635,9 +637,9 @@ __global__ void __launch_bounds__(512, 2) k_step_d3q19_moms(const KParams P,
                                                                 const int* __restrict__ tiles)
 {
     extern __shared__ unsigned char smem_raw[];
-    int bx, by, bz;
-    block_of(P, tiles, bx, by, bz);
-    tile_d3q19_mom<PREC, IDX, true>(P, A, B, link, bx, by, bz, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+    int bx, by, z0, z1;
+    block_of(P, tiles, bx, by, z0, z1);
+    tile_d3q19_mom<PREC, IDX, true>(P, A, B, link, bx, by, z0, z1, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
 }
 
 // ------------------------------------------- TMA-staged moment march (variant 8)
@@ -771,7 +773,7 @@ template <int PREC, int WY>
 __device__ __forceinline__ void tile_d3q19_tma(const KParams& P, const CUtensorMap* map,
                                                const typename Store<PREC>::S* __restrict__ A,
                                                typename Store<PREC>::S* __restrict__ B,
-                                               const uint32_t* __restrict__ link, int bx, int by, int bz,
+                                               const uint32_t* __restrict__ link, int bx, int by, int z0, int z1,
                                                unsigned char* smem, int* status)
 {
     using T = float;
@@ -801,8 +803,6 @@ __device__ __forceinline__ void tile_d3q19_tma(const KParams& P, const CUtensorM
     }
     const int sxy = xs + nx * ys;
     const int np = (int)P.np;
-    const int z0 = bz * P.rows;
-    const int z1 = min(z0 + P.rows, nz);
     const int nplanes = z1 - z0 + 2;  // pulled planes z0-1 .. z1
     const Phys<T>& ph = phys<T>(P);
     const T psi_wall = ph.psi_wall;
@@ -926,9 +926,9 @@ __global__ void __launch_bounds__(32 * WY, WY <= 6 ? 3 : 2) k_step_d3q19_tma(con
                                                                               const int* __restrict__ tiles, int* status)
 {
     extern __shared__ __align__(1024) unsigned char smem_tma[];
-    int bx, by, bz;
-    block_of(P, tiles, bx, by, bz);
-    tile_d3q19_tma<PREC, WY>(P, &tmA, A, B, link, bx, by, bz, smem_tma, status);
+    int bx, by, z0, z1;
+    block_of(P, tiles, bx, by, z0, z1);
+    tile_d3q19_tma<PREC, WY>(P, &tmA, A, B, link, bx, by, z0, z1, smem_tma, status);
 }
 
 // ------------------------------------------------- pipelined variants (variant 3)
@@ -1047,8 +1047,8 @@ __global__ void __launch_bounds__(256, 2) k_step_d3q19_pipe(const KParams P,
                                                             const uint32_t* __restrict__ link,
                                                             const int* __restrict__ tiles)
 {
-    int bx, by, bz;
-    block_of(P, tiles, bx, by, bz);
+    int bx, by, z0, z1;
+    block_of(P, tiles, bx, by, z0, z1);
     using T = typename Store<PREC>::T;
     using L = Lat<1>;
     constexpr int Q = 19;
@@ -1077,8 +1077,6 @@ __global__ void __launch_bounds__(256, 2) k_step_d3q19_pipe(const KParams P,
         u.yp = (long long)b * nx;
     }
     const IDX sxy = (IDX)xs + (IDX)nx * (IDX)ys;
-    const int z0 = bz * P.rows;
-    const int z1 = min(z0 + P.rows, nz);
     const T psi_wall = phys<T>(P).psi_wall;
     bool c1 = false, c2 = false;  // planes k-1, k-2 collide here
 
@@ -1178,8 +1176,8 @@ __global__ void __launch_bounds__(256, 1) k_step_d3q19_async(const KParams P,
                                                              const uint32_t* __restrict__ link,
                                                              const int* __restrict__ tiles)
 {
-    int bx, by, bz;
-    block_of(P, tiles, bx, by, bz);
+    int bx, by, z0, z1;
+    block_of(P, tiles, bx, by, z0, z1);
     using S = typename Store<PREC>::S;
     using T = typename Store<PREC>::T;
     using L = Lat<1>;
@@ -1211,8 +1209,6 @@ __global__ void __launch_bounds__(256, 1) k_step_d3q19_async(const KParams P,
     }
     const IDX sxy = (IDX)xs + (IDX)nx * (IDX)ys;
     const IDX np = (IDX)P.np;
-    const int z0 = bz * P.rows;
-    const int z1 = min(z0 + P.rows, nz);
     const Phys<T>& ph = phys<T>(P);
     const T psi_wall = ph.psi_wall;
     // site kind of a plane for this thread: 0 outside/wall, 1 fluid, 2 port ghost
@@ -1396,9 +1392,9 @@ __global__ void __launch_bounds__(256, MINB) k_batch_d3q19(const BatchSlot* __re
         const S* src = (const S*)(odd ? sl.b : sl.a);
         S* dst = (S*)(odd ? sl.a : sl.b);
         if (sP.collision == LBCG_REG)
-            tile_d3q19_mom<PREC, int, false>(sP, src, dst, sl.link, it.x, it.y, it.z, reinterpret_cast<T*>(smem_raw));
+            tile_d3q19_mom<PREC, int, false>(sP, src, dst, sl.link, it.x, it.y, it.z * sP.rows, min(it.z * sP.rows + sP.rows, sP.nz), reinterpret_cast<T*>(smem_raw));
         else
-            tile_d3q19<PREC, false, int>(sP, src, dst, sl.link, it.x, it.y, it.z, reinterpret_cast<T*>(smem_raw));
+            tile_d3q19<PREC, false, int>(sP, src, dst, sl.link, it.x, it.y, it.z * sP.rows, min(it.z * sP.rows + sP.rows, sP.nz), reinterpret_cast<T*>(smem_raw));
     }
 }
 
