@@ -296,6 +296,7 @@ def main():
                     help="only time the FP64 oracle on C1 / C3 (1 and all host threads) and print that line")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-autotune", action="store_true", help="library default launch shape")
+    ap.add_argument("--launch", default=None, help="rows,block_rows,variant: this launch shape (no autotuning)")
     ap.add_argument("--serving-requests", type=int, default=64, help="0 disables the serving sample")
     ap.add_argument("--serving-steps-scale", type=float, default=0.25)
     ap.add_argument("--serving-baseline", type=int, default=6)
@@ -341,7 +342,10 @@ def main():
     # ---------------------------------------------------------------- launch shape (untimed)
     shape = {}
     tuned = None
-    if not args.no_autotune:
+    if args.launch:
+        r_, b_, v_ = (int(t) for t in args.launch.split(","))
+        shape = {"rows": r_, "block_rows": b_, "variant": v_}
+    elif not args.no_autotune:
         from paper_1711_02003_gb300 import autotune
         tuned = autotune.autotune(pb, prec)
         shape = {k: tuned[k] for k in ("rows", "block_rows", "variant")}

@@ -309,8 +309,8 @@ int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
  * environment variable LBCG_TEST_PIPELINE_STALL=1 is set makes every pipeline wait of
  * variant 8 run out (failure-path test): the step then leaves the state invalid and
  * lbcg_synchronize and the read-back calls report LBCG_ERR_CUDA once.  The default is the
- * plain march for D2Q9; for D3Q19 with the regularized collision variant 7 (FP64: 6),
- * with BGK variant 5 (FP64: 2).  Within one variant results are bit-identical across
+ * plain march for D2Q9; for D3Q19 with the regularized collision variant 6, with BGK
+ * variant 5 (FP64: 2).  Within one variant results are bit-identical across
  * shapes; variants may contract multiply-adds and order sums differently and agree to
  * rounding.  Drops captured step graphs. */
 int lbcg_set_launch(lbcg_ctx* ctx, int rows, int block_rows, int variant);

@@ -1609,11 +1609,10 @@ int effective_variant(const lbcg_ctx* c)
 {
     const int prec = c->p.precision;
     if (c->p.lattice == LBCG_D2Q9) return c->variant == 3 ? 3 : 0;
-    // default (measured fastest): the moment march, with its moments in shared memory for
-    // 4- and 2-byte storage and in registers for FP64; the BGK update needs the individual
-    // populations and re-reads them (three blocks per SM, FP64 two)
+    // default (measured fastest): the moment march with its moments in registers; the BGK
+    // update needs the individual populations and re-reads them (three blocks per SM, FP64 two)
     const bool reg = c->p.collision == LBCG_REG;
-    int v = c->variant != 0 ? c->variant : (reg ? (prec == LBCG_FP64 ? 6 : 7) : (prec == LBCG_FP64 ? 2 : 5));
+    int v = c->variant != 0 ? c->variant : (reg ? 6 : (prec == LBCG_FP64 ? 2 : 5));
     if (v == 8 && !tma_supported(c)) v = prec == LBCG_FP64 ? 6 : 7;
     if ((v == 6 || v == 7) && !reg) v = prec == LBCG_FP64 ? 2 : 5;
     if (v == 4 && prec != LBCG_FP32 && prec != LBCG_FP32_DEV) v = 2;
