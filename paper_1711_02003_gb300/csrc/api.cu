@@ -174,6 +174,50 @@ void fill_kparams(lbcg_ctx* c)
 
 // active-tile list of the current launch shape (walled geometries): tiles (2D strips of
 // 30 x rows, 3D blocks of 30 x (block_rows-2) x rows) holding at least one fluid site
+// D3Q19 block tiles of launch shape k (30 x ty sites per x-y column) that hold fluid:
+// for each column, the planes holding a fluid site grouped in runs of consecutive planes,
+// each run cut into near-equal z-ranges of at most k.rows planes (a terrace 8 planes high
+// gets two ranges of 4, not a range of 4 and one of 4 holding one fluid plane).  Appends
+// (column index, z0 | z1 << 16) pairs ordered by range, then column.  False if nz > 65535.
+bool fitted_tiles_3d(const lbcg_ctx* c, const KParams& k, int ty, std::vector<int>& list)
+{
+    const int nx = c->dims[0], ny = c->dims[1], nz = c->dims[2];
+    if (nz > 0xffff) return false;
+    const long long ncol = (long long)k.nsx * k.nsy;
+    std::vector<char> has((size_t)(ncol * nz), 0);
+    for (long long s = 0; s < c->n; ++s) {
+        if (c->mask[s] != LBCG_MASK_FLUID) continue;
+        const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
+        has[(size_t)(((x / 30) + (long long)k.nsx * (y / ty)) * nz + z)] = 1;
+    }
+    std::vector<std::vector<std::pair<int, int>>> ranges((size_t)ncol);
+    size_t depth = 0;
+    for (long long col = 0; col < ncol; ++col) {
+        const char* h = &has[(size_t)(col * nz)];
+        for (int z = 0; z < nz;) {
+            if (!h[z]) {
+                ++z;
+                continue;
+            }
+            int e = z;
+            while (e < nz && h[e]) ++e;
+            const int len = e - z, parts = (len + k.rows - 1) / k.rows;
+            for (int q = 0; q < parts; ++q)
+                ranges[(size_t)col].push_back(
+                    {z + (int)((long long)len * q / parts), z + (int)((long long)len * (q + 1) / parts)});
+            z = e;
+        }
+        depth = std::max(depth, ranges[(size_t)col].size());
+    }
+    for (size_t d = 0; d < depth; ++d)
+        for (long long col = 0; col < ncol; ++col)
+            if (d < ranges[(size_t)col].size()) {
+                list.push_back((int)col);
+                list.push_back(ranges[(size_t)col][d].first | (ranges[(size_t)col][d].second << 16));
+            }
+    return true;
+}
+
 int build_tiles(lbcg_ctx* c)
 {
     cudaFree(c->d_tiles);
@@ -198,45 +242,7 @@ int build_tiles(lbcg_ctx* c)
         if ((long long)list.size() == ntot) return LBCG_OK;  // nothing to skip
         if (list.empty()) list.push_back(0);
     } else {
-        // for each x-y column of 30 x (block_rows - 2) sites: the planes holding a fluid site,
-        // grouped in runs of consecutive planes, each run cut into near-equal z-ranges of at
-        // most `rows` planes (a terrace 8 planes high gets two ranges of 4, not a range of 4
-        // and one of 4 holding one fluid plane); entries (column, z0 | z1 << 16) ordered by
-        // range, then column
-        if (nz > 0xffff) return fail(LBCG_ERR_GEOMETRY, "nz above 65535 with walls");
-        const int ty = c->block_rows - 2;
-        const long long ncol = (long long)k.nsx * k.nsy;
-        std::vector<char> has((size_t)(ncol * nz), 0);
-        for (long long s = 0; s < c->n; ++s) {
-            if (c->mask[s] != LBCG_MASK_FLUID) continue;
-            const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
-            has[(size_t)(((x / 30) + (long long)k.nsx * (y / ty)) * nz + z)] = 1;
-        }
-        std::vector<std::vector<std::pair<int, int>>> ranges((size_t)ncol);
-        size_t depth = 0;
-        for (long long col = 0; col < ncol; ++col) {
-            const char* h = &has[(size_t)(col * nz)];
-            for (int z = 0; z < nz;) {
-                if (!h[z]) {
-                    ++z;
-                    continue;
-                }
-                int e = z;
-                while (e < nz && h[e]) ++e;
-                const int len = e - z, parts = (len + k.rows - 1) / k.rows;
-                for (int q = 0; q < parts; ++q)
-                    ranges[(size_t)col].push_back({z + (int)((long long)len * q / parts),
-                                                   z + (int)((long long)len * (q + 1) / parts)});
-                z = e;
-            }
-            depth = std::max(depth, ranges[(size_t)col].size());
-        }
-        for (size_t d = 0; d < depth; ++d)
-            for (long long col = 0; col < ncol; ++col)
-                if (d < ranges[(size_t)col].size()) {
-                    list.push_back((int)col);
-                    list.push_back(ranges[(size_t)col][d].first | (ranges[(size_t)col][d].second << 16));
-                }
+        if (!fitted_tiles_3d(c, k, c->block_rows - 2, list)) return fail(LBCG_ERR_GEOMETRY, "nz above 65535 with walls");
         if (list.empty()) {
             list.push_back(0);
             list.push_back(0);  // an empty range: the block pulls ring planes only

@@ -30,6 +30,7 @@ struct lbcg_batch {
     std::vector<long long> remaining;     // steps still to run
     std::vector<char> reported;           // completion already returned by poll
     std::vector<KParams> kp;              // per-slot launch-shaped parameters
+    std::vector<std::vector<int>> tiles;  // per-slot D3Q19 fitted tiles (column, z-range), set at add
     BatchSlot* h_slots = nullptr;         // pinned, two tables (replays alternate between them)
     BatchSlot* d_slots = nullptr;
     std::vector<BatchItem> h_items, h_fill;
@@ -71,9 +72,10 @@ int rebuild(lbcg_batch* b)
             const int strips = k.nsx * k.nsy;
             for (int f = 0; f < strips; f += 8) b->h_items.push_back({s, f, std::min(8, strips - f), 0});
         } else {
-            for (int z = 0; z < k.nsz; ++z)
-                for (int y = 0; y < k.nsy; ++y)
-                    for (int x = 0; x < k.nsx; ++x) b->h_items.push_back({s, x, y, z});
+            // the instance's block tiles that hold fluid, with fitted z-ranges (computed at add)
+            const std::vector<int>& tiles = b->tiles[s];
+            for (size_t t = 0; t + 1 < tiles.size(); t += 2)
+                b->h_items.push_back({s, tiles[t] % k.nsx, tiles[t] / k.nsx, tiles[t + 1]});
         }
         const int ng = b->ctx[s]->nghost;
         for (int f = 0; f < ng; f += 64) b->h_fill.push_back({s, f, std::min(64, ng - f), 0});  // a thread per ghost
@@ -156,6 +158,7 @@ int lbcg_batch_create(int lattice, int precision, int max_instances, void* strea
     b->remaining.assign(max_instances, 0);
     b->reported.assign(max_instances, 0);
     b->kp.resize(max_instances);
+    b->tiles.resize(max_instances);
     bool ok = cudaMallocHost(&b->h_slots, 2 * sizeof(BatchSlot) * max_instances) == cudaSuccess &&
               cudaMalloc(&b->d_slots, sizeof(BatchSlot) * max_instances) == cudaSuccess &&
               cudaMalloc(&b->d_counts, 2 * sizeof(int)) == cudaSuccess &&
@@ -210,6 +213,12 @@ int lbcg_batch_add(lbcg_batch* b, lbcg_ctx* c, long long steps, int* slot)
     b->remaining[s] = steps;
     b->reported[s] = 0;
     b->kp[s] = make_kparams(c->p, c->dims, c->np, b->lattice == LBCG_D2Q9 ? kBatch2DRows : 8, 8);
+    b->tiles[s].clear();
+    if (b->lattice != LBCG_D2Q9 && !fitted_tiles_3d(c, b->kp[s], 8 - 2, b->tiles[s])) {
+        b->ctx[s] = nullptr;
+        b->remaining[s] = 0;
+        return bfail(LBCG_ERR_CAPACITY, "instance with nz above 65535 in a batch");
+    }
     b->dirty = true;
     *slot = s;
     return LBCG_OK;

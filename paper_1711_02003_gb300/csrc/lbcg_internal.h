@@ -68,7 +68,8 @@ struct BatchSlot {
     int nghost;
     int steps;               // steps this launch advances the instance (0 = idle)
 };
-// work item: D2Q9 (slot, first strip, strip count <= 8, -); D3Q19 (slot, bx, by, bz);
+// work item: D2Q9 (slot, first strip, strip count <= 8, -); D3Q19 (slot, bx, by, z0 | z1 << 16)
+// over the instance's fitted tiles;
 // port refill (slot, first ghost, ghost count <= 64, -)
 struct BatchItem {
     int slot, x, y, z;
@@ -171,6 +172,7 @@ cudaError_t launch_batch_fill(int lattice, int precision, const BatchSlot* slots
 
 void fill_kparams(lbcg_ctx* c);
 int build_tiles(lbcg_ctx* c);
+bool fitted_tiles_3d(const lbcg_ctx* c, const KParams& k, int ty, std::vector<int>& list);
 // noalloc.cu
 int noalloc_observables(const lbcg_params* p, const void* state, const uint8_t* mask, const double centre[3],
                         double r_in, double r_out, void* stream, lbcg_obs* out, std::string& err);

@@ -1392,9 +1392,9 @@ __global__ void __launch_bounds__(256, MINB) k_batch_d3q19(const BatchSlot* __re
         const S* src = (const S*)(odd ? sl.b : sl.a);
         S* dst = (S*)(odd ? sl.a : sl.b);
         if (sP.collision == LBCG_REG)
-            tile_d3q19_mom<PREC, int, false>(sP, src, dst, sl.link, it.x, it.y, it.z * sP.rows, min(it.z * sP.rows + sP.rows, sP.nz), reinterpret_cast<T*>(smem_raw));
+            tile_d3q19_mom<PREC, int, false>(sP, src, dst, sl.link, it.x, it.y, it.z & 0xffff, it.z >> 16, reinterpret_cast<T*>(smem_raw));
         else
-            tile_d3q19<PREC, false, int>(sP, src, dst, sl.link, it.x, it.y, it.z * sP.rows, min(it.z * sP.rows + sP.rows, sP.nz), reinterpret_cast<T*>(smem_raw));
+            tile_d3q19<PREC, false, int>(sP, src, dst, sl.link, it.x, it.y, it.z & 0xffff, it.z >> 16, reinterpret_cast<T*>(smem_raw));
     }
 }
 
