@@ -62,7 +62,8 @@ enum lbcg_status {
     LBCG_ERR_DIVERGED = -5,  /* non-finite or non-positive density found */
     LBCG_ERR_GEOMETRY = -6,  /* invalid mask / port table */
     LBCG_ERR_CAPACITY = -7,  /* caller buffer too small */
-    LBCG_ERR_UNSUPPORTED = -8
+    LBCG_ERR_UNSUPPORTED = -8,
+    LBCG_ERR_TIMEOUT = -9      /* a bounded device-side wait or iteration ran out (state invalid) */
 };
 
 enum lbcg_lattice { LBCG_D2Q9 = 0, LBCG_D3Q19 = 1 };
@@ -243,7 +244,8 @@ int lbcg_observables_noalloc(const lbcg_params* p, const void* dev_state, const 
  * smallest linear site index of the site's component, or -1.  counts/volumes (may be
  * NULL) receive, in increasing label order, each droplet's site count and its
  * sum of (1+psi)/2, for at most cap droplets; *n_drops receives the total number.
- * Synchronous. */
+ * Synchronous.  The union-find passes are bounded: LBCG_ERR_TIMEOUT if the bound is
+ * reached (labels then invalid). */
 int lbcg_label(lbcg_ctx* ctx, int32_t* labels, int64_t* counts, double* volumes, int cap, int* n_drops);
 
 /* ------------------------------------------------------------------ batches
@@ -308,7 +310,7 @@ int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
  * fall back to 5 (FP64: 2) for the BGK collision.  A context created while the
  * environment variable LBCG_TEST_PIPELINE_STALL=1 is set makes every pipeline wait of
  * variant 8 run out (failure-path test): the step then leaves the state invalid and
- * lbcg_synchronize and the read-back calls report LBCG_ERR_CUDA once.  The default is the
+ * lbcg_synchronize and the read-back calls report LBCG_ERR_TIMEOUT once.  The default is the
  * plain march for D2Q9; for D3Q19 with the regularized collision variant 6, with BGK
  * variant 5 (FP64: 2).  Within one variant results are bit-identical across
  * shapes; variants may contract multiply-adds and order sums differently and agree to

@@ -287,6 +287,7 @@ const char* lbcg_strerror(int s)
         case LBCG_ERR_GEOMETRY: return "invalid geometry";
         case LBCG_ERR_CAPACITY: return "output capacity too small";
         case LBCG_ERR_UNSUPPORTED: return "unsupported";
+        case LBCG_ERR_TIMEOUT: return "bounded wait or iteration ran out";
         default: return "unknown status";
     }
 }
@@ -731,7 +732,7 @@ static int check_status(lbcg_ctx* c)
     LBCG_CUDA(cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
     if (h == 0) return LBCG_OK;
     LBCG_CUDA(cudaMemset(c->d_status, 0, sizeof(int)), "status reset");
-    return fail(LBCG_ERR_CUDA, "step kernel: a shared-memory pipeline wait timed out; the state is invalid");
+    return fail(LBCG_ERR_TIMEOUT, "step kernel: a shared-memory pipeline wait timed out; the state is invalid");
 }
 
 int lbcg_synchronize(lbcg_ctx* c)
@@ -958,7 +959,7 @@ int lbcg_label(lbcg_ctx* c, int32_t* labels, int64_t* counts, double* volumes, i
     LBCG_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy flag");
     LBCG_CUDA(cudaStreamSynchronize(c->stream), "label sync");
     if (const int st_ = check_status(c)) return st_;
-    if (hflag) return fail(LBCG_ERR_CUDA, "labelling iteration bound reached");
+    if (hflag) return fail(LBCG_ERR_TIMEOUT, "labelling iteration bound reached");
     // per-droplet count and volume in label order, sums in site order
     std::vector<int> slot(n, -1);
     int nd = 0;

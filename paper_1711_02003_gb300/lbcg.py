@@ -24,6 +24,7 @@ LBCG_OK = 0
 LBCG_D2Q9, LBCG_D3Q19 = 0, 1
 LBCG_FP64, LBCG_FP32, LBCG_FP32_DEV, LBCG_FP16_SCALED = 0, 1, 2, 3
 LBCG_REG, LBCG_BGK = 0, 1
+LBCG_ERR_TIMEOUT = -9  # a bounded device-side wait or iteration ran out
 PRECISION_NAMES = {LBCG_FP64: "f64", LBCG_FP32: "f32", LBCG_FP32_DEV: "f32dev", LBCG_FP16_SCALED: "f16scaled"}
 ELEM_BYTES = {LBCG_FP64: 8, LBCG_FP32: 4, LBCG_FP32_DEV: 4, LBCG_FP16_SCALED: 2}
 

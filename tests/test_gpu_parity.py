@@ -189,8 +189,9 @@ def test_tma_pipeline_timeout_is_reported(monkeypatch):
     bad = lb.Simulation(prob, lb.LBCG_FP32_DEV, variant=8)
     monkeypatch.delenv("LBCG_TEST_PIPELINE_STALL")
     bad.step(1)
-    with pytest.raises(lb.LbcgError, match="timed out"):
+    with pytest.raises(lb.LbcgError, match="timed out") as err:
         bad.synchronize()
+    assert err.value.status == lb.LBCG_ERR_TIMEOUT
     bad.synchronize()  # reported once
     good = lb.Simulation(prob, lb.LBCG_FP32_DEV, variant=8)
     ref = lb.Simulation(prob, lb.LBCG_FP32_DEV, variant=7)
@@ -349,6 +350,20 @@ def test_full_size_flow_focuser_fp64_sampled():
     pb = W.cross_junction(u_disp=0.005, u_cont=0.005)
     g, o = run_pair(pb, 20, lb.LBCG_FP64)
     assert np.abs(g.populations() - o.populations()).max() <= 1e-12
+
+
+def test_full_size_laplace_box():
+    """128^3 periodic droplet box of the 3D Laplace sweep (R = 16), in the default launch shape:
+    FP64 populations at every site after 4 steps, FP32-dev fields after 4 steps."""
+    lb = _lb()
+    pb = W.static_droplet(W.D3Q19, 128, 16)
+    g, o = run_pair(pb, 4, lb.LBCG_FP64)
+    assert np.abs(g.populations() - o.populations()).max() <= 1e-12
+    g32 = lb.Simulation(pb, lb.LBCG_FP32_DEV)
+    g32.step(4)
+    gr, gb, gu = g32.fields()
+    orr, ob, ou = o.fields()
+    assert relmax(gr, orr) <= 1e-6 and relmax(gb, ob) <= 1e-6
 
 
 def test_full_size_step_emulsifier_fp32dev():
