@@ -306,10 +306,15 @@ int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
  * 8 (D3Q19, regularized, FP32 or FP32-dev storage, nx a multiple of 4, block_rows 6 or
  * 8) the moment march with every plane's pulled populations staged in shared memory by
  * the tensor memory accelerator (two-stage pipeline of Q boxes per plane, bounded
- * waits); where its conditions do not hold it runs as 7 (FP64: 6).  Variants 6 and 7
- * fall back to 5 (FP64: 2) for the BGK collision.  A context created while the
+ * waits); where its conditions do not hold it runs as 7 (FP64: 6).  10 (D3Q19,
+ * regularized, 4- or 2-byte storage, box closed in x and y) psi-exchange march: tiles of
+ * 32 x block_rows sites with no ring lanes or rows; each tile publishes psi of its planes
+ * (per-site buffer and per-plane flags) and reads its x-y ring from its neighbour tiles
+ * after bounded waits; persistent blocks take tiles in order; it runs as 6 where its
+ * conditions or its forward-progress bound (enough resident blocks) do not hold.
+ * Variants 6 and 7 fall back to 5 (FP64: 2) for the BGK collision.  A context created while the
  * environment variable LBCG_TEST_PIPELINE_STALL=1 is set makes every pipeline wait of
- * variant 8 run out (failure-path test): the step then leaves the state invalid and
+ * variants 8 and 10 run out (failure-path test): the step then leaves the state invalid and
  * lbcg_synchronize and the read-back calls report LBCG_ERR_TIMEOUT once.  The default is the
  * plain march for D2Q9; for D3Q19 with the regularized collision variant 6, with BGK
  * variant 5 (FP64: 2).  Within one variant results are bit-identical across

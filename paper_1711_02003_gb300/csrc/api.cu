@@ -218,7 +218,102 @@ bool fitted_tiles_3d(const lbcg_ctx* c, const KParams& k, int ty, std::vector<in
     return true;
 }
 
+static void free_xchg(lbcg_ctx* c)
+{
+    cudaFree(c->d_xtiles);
+    cudaFree(c->d_xmap);
+    cudaFree(c->d_psibuf);
+    cudaFree(c->d_xflags);
+    cudaFree(c->d_xctl);
+    c->d_xtiles = c->d_xmap = c->d_xflags = c->d_xctl = nullptr;
+    c->d_psibuf = nullptr;
+    c->xntiles = c->xgrid = 0;
+}
+
+// Tiles of the psi-exchange march (variant 10, when asked for) for boxes closed in x and y
+// with the regularized collision in 4- or 2-byte storage: 32 x block_rows interior sites per tile,
+// uniform z-slabs of `rows` planes; a tile is listed when a fluid or port site lies in its
+// planes z0 - 1 .. z1 (its pulled planes), so every neighbour whose psi a listed tile reads
+// publishes it in the same step.  Order: slab, then column.
+static int build_xchg(lbcg_ctx* c)
+{
+    free_xchg(c);
+    const int prec = c->p.precision;
+    if (c->variant != 10 || c->p.lattice != LBCG_D3Q19 || c->p.collision != LBCG_REG || prec == LBCG_FP64 ||
+        c->p.periodic[0] || c->p.periodic[1] || !c->geometry || !c->any_link || c->block_rows > 8)
+        return LBCG_OK;  // built only when the psi-exchange march is asked for
+    const int nx = c->dims[0], ny = c->dims[1], nz = c->dims[2];
+    const int wy = c->block_rows, rows = c->kp.rows;
+    const int xnsx = (nx + 31) / 32, xnsy = (ny + wy - 1) / wy, xnsz = (nz + rows - 1) / rows;
+    const long long ncol = (long long)xnsx * xnsy;
+    std::vector<char> plane((size_t)(ncol * nz), 0);  // column has a fluid or port site in plane z
+    for (long long s = 0; s < c->n; ++s) {
+        const uint8_t m = c->mask[s];
+        if (m == LBCG_MASK_WALL) continue;
+        const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
+        plane[(size_t)(((x / 32) + (long long)xnsx * (y / wy)) * nz + z)] = 1;
+    }
+    std::vector<int> tiles, map((size_t)(ncol * xnsz), -1);
+    for (int sl = 0; sl < xnsz; ++sl) {
+        const int z0 = sl * rows, z1 = std::min(z0 + rows, nz);
+        for (long long col = 0; col < ncol; ++col) {
+            bool on = false;
+            for (int z = z0 - 1; z <= z1 && !on; ++z) {
+                int zs = z;
+                if (z < 0 || z >= nz) {
+                    if (!c->p.periodic[2]) continue;
+                    zs = z < 0 ? z + nz : z - nz;
+                }
+                on = plane[(size_t)(col * nz + zs)] != 0;
+            }
+            if (!on) continue;
+            map[(size_t)(sl * ncol + col)] = (int)(tiles.size() / 2);
+            tiles.push_back((int)col);
+            tiles.push_back(sl);
+        }
+    }
+    if (tiles.empty()) return LBCG_OK;
+    const int nt = (int)(tiles.size() / 2);
+    std::vector<float> psi((size_t)c->n, (float)c->p.psi_wall);
+    const int ctl[4] = {0, 0, 1, 0};
+    bool ok = cudaMalloc(&c->d_xtiles, sizeof(int) * tiles.size()) == cudaSuccess &&
+              cudaMalloc(&c->d_xmap, sizeof(int) * map.size()) == cudaSuccess &&
+              cudaMalloc(&c->d_psibuf, sizeof(float) * (size_t)c->n) == cudaSuccess &&
+              cudaMalloc(&c->d_xflags, sizeof(int) * (size_t)nt * (rows + 2)) == cudaSuccess &&
+              cudaMalloc(&c->d_xctl, sizeof(ctl)) == cudaSuccess;
+    if (!ok) {
+        free_xchg(c);
+        return fail(LBCG_ERR_NOMEM, "exchange tables allocation failed");
+    }
+    ok = cudaMemcpy(c->d_xtiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(c->d_xmap, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(c->d_psibuf, psi.data(), sizeof(float) * psi.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(c->d_xflags, 0, sizeof(int) * (size_t)nt * (rows + 2)) == cudaSuccess &&
+         cudaMemcpy(c->d_xctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        free_xchg(c);
+        return fail(LBCG_ERR_CUDA, "exchange tables copy failed");
+    }
+    c->xnsx = xnsx;
+    c->xnsy = xnsy;
+    c->xnsz = xnsz;
+    c->xntiles = nt;
+    c->xrows = rows;
+    c->xwy = wy;
+    c->xgrid = xchg_resident_blocks(c);
+    return LBCG_OK;
+}
+
+static int build_active_tiles(lbcg_ctx* c);
+
 int build_tiles(lbcg_ctx* c)
+{
+    const int st = build_active_tiles(c);
+    if (st) return st;
+    return build_xchg(c);
+}
+
+static int build_active_tiles(lbcg_ctx* c)
 {
     cudaFree(c->d_tiles);
     c->d_tiles = nullptr;
@@ -360,6 +455,7 @@ void lbcg_destroy(lbcg_ctx* c)
     cudaFree(c->d_partials);
     cudaFree(c->d_result);
     cudaFree(c->d_status);
+    free_xchg(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
@@ -732,7 +828,7 @@ static int check_status(lbcg_ctx* c)
     LBCG_CUDA(cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
     if (h == 0) return LBCG_OK;
     LBCG_CUDA(cudaMemset(c->d_status, 0, sizeof(int)), "status reset");
-    return fail(LBCG_ERR_TIMEOUT, "step kernel: a shared-memory pipeline wait timed out; the state is invalid");
+    return fail(LBCG_ERR_TIMEOUT, "step kernel: a bounded wait timed out; the state is invalid");
 }
 
 int lbcg_synchronize(lbcg_ctx* c)
@@ -1027,9 +1123,9 @@ int lbcg_set_launch(lbcg_ctx* c, int rows, int block_rows, int variant)
     // blocks of up to 512 threads; every other kernel up to 256
     const int max_wy = variant == 7 && c->p.collision == LBCG_REG ? 16 : 8;
     if (rows < 0 || block_rows < 0 || (block_rows > 0 && (block_rows < 3 || block_rows > max_wy)) || variant < 0 ||
-        variant > 8)
+        variant > 10 || variant == 9)
         return fail(LBCG_ERR_ARG,
-                    "launch shape out of range (block_rows in 3..8, 3..16 with variant 7; variant in 0..8)");
+                    "launch shape out of range (block_rows in 3..8, 3..16 with variant 7; variant in 0..8, 10)");
     c->rows = rows;
     c->block_rows = block_rows;
     c->variant = variant;

@@ -146,6 +146,18 @@ struct lbcg_ctx {
     int* d_status = nullptr;
     int stall_test = 0;  // LBCG_TEST_PIPELINE_STALL set when the context was created
 
+    // psi-exchange step kernel (variant 10): tiles of 32 x block_rows interior sites in
+    // uniform z-slabs of `rows` planes that hold a fluid or port site, ordered by slab then
+    // column; map (slab, column) -> tile index or -1; per-site psi published by the tiles;
+    // per-tile, per-plane flags holding the step epoch; control words (tile counter, blocks
+    // done, epoch)
+    int* d_xtiles = nullptr;
+    int* d_xmap = nullptr;
+    float* d_psibuf = nullptr;
+    int* d_xflags = nullptr;
+    int* d_xctl = nullptr;
+    int xnsx = 0, xnsy = 0, xnsz = 0, xntiles = 0, xrows = 0, xwy = 0, xgrid = 0;
+
     lbcg::KParams kp;
 };
 
@@ -155,6 +167,8 @@ namespace lbcg {
 cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b);
 int effective_variant(const lbcg_ctx* c);  // the step kernel variant launch_step runs
 bool tma_supported(const lbcg_ctx* c);     // the TMA-staged variant applies to this context
+int xchg_resident_blocks(const lbcg_ctx* c);  // persistent grid of the psi-exchange march
+bool xchg_supported(const lbcg_ctx* c);       // the psi-exchange march applies (tables built, progress bound)
 // launchers (aux.cu)
 cudaError_t launch_fill_ports(lbcg_ctx* c, void* a);
 cudaError_t launch_init(lbcg_ctx* c, const double* rr, const double* rb, const double* u, void* a);

@@ -931,6 +931,223 @@ __global__ void __launch_bounds__(32 * WY, WY <= 6 ? 3 : 2) k_step_d3q19_tma(con
     tile_d3q19_tma<PREC, WY>(P, &tmA, A, B, link, bx, by, z0, z1, smem_tma, status);
 }
 
+// --------------------------------------- psi-exchange moment march (variant 10)
+// The psi ring of a block tile is the one quantity the tile cannot compute from its own
+// sites; the other marches recompute it by pulling the ring sites' 2Q populations (32 x WY
+// threads pull for 30 x (WY - 2) collided sites).  Here every thread owns an interior site
+// (tiles of 32 x WY) and the tiles exchange psi instead: after summing plane z a tile
+// publishes psi of its sites (per-site buffer, then its flag for that plane = the step's
+// epoch), waits for the flags of its eight x-y neighbour tiles for the same plane and
+// reads their edge psi from L2.  z-ring planes are still pulled (tiles of one x-y column
+// are in different slabs).  Blocks are persistent and take tiles in list order (slab, then
+// column); a tile is at most one plane ahead of its neighbours, so with more than
+// (nsx + 2)(rows + 2) resident blocks the oldest tile always completes (checked on the
+// host, else variant 6 runs).  Waits are bounded: on a timeout the status word is set,
+// every other wait gives up at once, the step completes with an invalid state and the host
+// reports LBCG_ERR_TIMEOUT.  The last block to finish resets the tile counter and advances
+// the epoch, so replays of a captured graph need no host involvement.  Regularized
+// collision, 4- and 2-byte storage, boxes closed in x and y.
+struct XParams {
+    int nsx, nsy, ntiles, rows;
+    const int* tiles;  // [ntiles][2]: column bx + nsx * by, slab
+    const int* map;    // [slab][column]: tile index or -1 (no fluid or port in its planes)
+    float* psi;        // per-site psi of the current step (psi_wall where never written)
+    int* flags;        // [ntiles][rows + 2]: epoch of the last publication of each plane
+    int* ctl;          // [0] next tile, [1] blocks done, [2] epoch
+    int* status;       // nonzero: a wait timed out (every later wait gives up)
+};
+
+constexpr int kXWaitLimit = 1 << 16;  // polls of a neighbour flag (32 ns sleeps) before giving up
+
+template <int PREC>
+__global__ void __launch_bounds__(256, 4) k_step_d3q19_xchg(const KParams P, const XParams X,
+                                                            const typename Store<PREC>::S* __restrict__ A,
+                                                            typename Store<PREC>::S* __restrict__ B,
+                                                            const uint32_t* __restrict__ link)
+{
+    using T = typename Store<PREC>::T;
+    using SP = Store<PREC>;
+    using L = Lat<1>;
+    constexpr int Q = 19;
+    extern __shared__ unsigned char smem_raw[];
+    T* const ring = reinterpret_cast<T*>(smem_raw);  // [8][WY + 2][34]
+    __shared__ int s_tile;
+    const int lane = threadIdx.x, w = threadIdx.y, WY = blockDim.y, tid = w * 32 + lane;
+    const int RW = 34, RH = WY + 2;
+    const int mstride = WY * 32;
+    T* const mom = ring + 8 * RH * RW + tid;  // [plane mod 3][11][WY * 32], thread-private
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const int nxy = nx * ny;
+    const int np = (int)P.np;
+    const Phys<T>& ph = phys<T>(P);
+    const T psi_wall = ph.psi_wall;
+    const int epoch = *(volatile const int*)(X.ctl + 2);
+    const int nplanes_max = X.rows + 2;
+
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(X.ctl, 1);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= X.ntiles) break;
+        const int col = X.tiles[2 * t], slab = X.tiles[2 * t + 1];
+        const int bx = col % X.nsx, by = col / X.nsx;
+        const int x0 = bx * 32, y0 = by * WY;
+        const int x = x0 + lane, y = y0 + w;
+        const bool inb = x < nx && y < ny;
+        const int xs = inb ? x : 0, ys = inb ? y : 0;
+        Up u;
+        {
+            int a, b;
+            nbr_off(xs, nx, 0, u.xm, u.xp);
+            nbr_off(ys, ny, 0, a, b);
+            u.ym = (long long)a * nx;
+            u.yp = (long long)b * nx;
+        }
+        const int sxy = xs + nx * ys;
+        const int z0 = slab * X.rows, z1 = min(z0 + X.rows, nz);
+        const int nplanes = z1 - z0 + 2;
+        // waiter lanes 0..7 of the last warp: the eight x-y neighbour tiles of the same slab
+        int nbt = -1;
+        if (w == WY - 1 && lane < 8) {
+            const int dx = lane < 3 ? lane - 1 : (lane == 3 ? -1 : (lane == 4 ? 1 : lane - 6));
+            const int dy = lane < 3 ? -1 : (lane < 5 ? 0 : 1);
+            const int nbx = bx + dx, nby = by + dy;
+            if (nbx >= 0 && nbx < X.nsx && nby >= 0 && nby < X.nsy)
+                nbt = X.map[(size_t)slab * X.nsx * X.nsy + nbx + X.nsx * nby];
+        }
+
+        // iteration k pulls plane z0 - 1 + k, publishes it, collides plane z0 - 3 + k (its
+        // ring planes are complete) and only then waits for the neighbours' plane k and
+        // fetches its ring edge: one barrier per plane, the wait overlapping the collision
+        unsigned coll_bits = 0;  // bit k: plane z0 - 1 + k is collided by this thread
+#pragma unroll 1
+        for (int k = 0; k <= nplanes; ++k) {
+            const int zz = z0 - 1 + k;
+            const bool pulling = k < nplanes;
+            int zs = 0;
+            const bool zok = pulling && wrap_coord(zz, nz, P.per[2], zs);
+            const int slot = k & 7;
+            if (pulling) {
+                {
+                    int a, b;
+                    nbr_off(zs, nz, P.per[2], a, b);
+                    u.zm = (long long)a * nxy;
+                    u.zp = (long long)b * nxy;
+                }
+                SiteMom<T> mn;
+                mom_zero(mn);
+                T psi_n = psi_wall;
+                bool fluid_n = false;
+                const int site = sxy + nxy * zs;
+                const bool full = zz >= z0 && zz < z1;
+                if (inb && zok) {
+                    const uint32_t lk = __ldg(link + site);
+                    const uint32_t type = (lk >> kTypeShift) & 3u;
+                    if (type == kTypeFluid) {
+                        psi_n = full ? pull_moments<1, PREC, int, true>(P, A, site, u, lk, mn)
+                                     : pull_moments<1, PREC, int, false>(P, A, site, u, lk, mn);
+                        fluid_n = true;
+                    } else if (type == kTypePort) {
+                        psi_n = ghost_psi<1, PREC, int>(P, A, site);
+                    }
+                    X.psi[site] = (float)psi_n;
+                }
+                ring[(slot * RH + w + 1) * RW + lane + 1] = psi_n;
+                if (fluid_n && inb && full) {
+                    mom_put(mn, mom + (k % 3) * 11 * mstride, mstride);
+                    coll_bits |= 1u << k;
+                }
+            }
+            __syncthreads();
+            if (pulling && tid == 0) {
+                __threadfence();
+                atomicExch(X.flags + (size_t)t * nplanes_max + k, epoch);
+            }
+            // collide plane z0 - 3 + k: psi of its planes z0 - 4 + k .. z0 - 2 + k is complete
+            if (k >= 3 && (coll_bits >> (k - 2) & 1u)) {
+                const int kc = k - 2;
+                const int zc = z0 - 1 + kc;
+                const int sc = sxy + nxy * zc;
+                auto nb = [&](int cx, int cy, int cz) -> T {
+                    return ring[(((kc + cz) & 7) * RH + (w + 1 + cy)) * RW + (lane + 1 + cx)];
+                };
+                T F[3] = {T(0), T(0), T(0)};
+#pragma unroll
+                for (int kk = 0; kk < L::NP; ++kk) {
+                    const int p = L::rep(kk);
+                    const int cx = L::cx(p), cy = L::cy(p), cz = L::cz(p);
+                    const T d = (T)L::w(p) * (nb(cx, cy, cz) - nb(-cx, -cy, -cz));
+                    if (cx) F[0] += cx > 0 ? d : -d;
+                    if (cy) F[1] += cy > 0 ? d : -d;
+                    if (cz) F[2] += cz > 0 ? d : -d;
+                }
+                F[0] *= T(3);
+                F[1] *= T(3);
+                F[2] *= T(3);
+                SiteMom<T> mb;
+                mom_get(mb, mom + (kc % 3) * 11 * mstride, mstride);
+                collide_moments<1, T>(ph, mb, F, [&](int i, T r, T g) {
+                    const int ir = i * np + sc;
+                    SP::store(B, ir, ir + Q * np, ph, L::cls(i), r, g);
+                });
+            }
+            if (pulling && w == WY - 1) {
+                // the last warp waits for the neighbours' plane k and fetches the ring edge
+                bool ok = true;
+                if (nbt >= 0) {
+                    const volatile int* f = X.flags + (size_t)nbt * nplanes_max + k;
+                    const int want = P.stall_test ? epoch + 1 : epoch;  // failure-path test: never published
+                    int it = 0;
+                    while (*f != want) {
+                        if (*(volatile int*)X.status != 0 || ++it > kXWaitLimit) {
+                            ok = false;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    __threadfence();
+                }
+                if (!ok) atomicExch(X.status, 2);
+                __syncwarp();
+                const int ncell = 2 * RW + 2 * WY;
+                for (int c = lane; c < ncell; c += 32) {
+                    int gx, gy, rr, rc;
+                    if (c < 2 * RW) {
+                        const int top = c < RW;
+                        rc = top ? c : c - RW;
+                        rr = top ? 0 : WY + 1;
+                        gx = x0 - 1 + rc;
+                        gy = top ? y0 - 1 : y0 + WY;
+                    } else {
+                        const int c2 = c - 2 * RW;
+                        const int left = c2 < WY;
+                        rr = (left ? c2 : c2 - WY) + 1;
+                        rc = left ? 0 : RW - 1;
+                        gx = left ? x0 - 1 : x0 + 32;
+                        gy = y0 + rr - 1;
+                    }
+                    T v = psi_wall;
+                    if (zok && gx >= 0 && gx < nx && gy >= 0 && gy < ny) v = (T)__ldcg(X.psi + gx + nx * gy + nxy * zs);
+                    ring[(slot * RH + rr) * RW + rc] = v;
+                }
+            }
+        }
+        __syncthreads();  // the ring and moment slots are reused by the next tile
+    }
+    // the last block to finish rearms the tile counter and advances the epoch
+    if (tid == 0) {
+        __threadfence();
+        const int d = atomicAdd(X.ctl + 1, 1);
+        if (d == (int)gridDim.x - 1) {
+            atomicExch(X.ctl, 0);
+            atomicExch(X.ctl + 1, 0);
+            __threadfence();
+            atomicAdd(X.ctl + 2, 1);
+        }
+    }
+}
+
 // ------------------------------------------------- pipelined variants (variant 3)
 // The collision of row/plane k needs psi of k+1, so a plain march waits for the loads of
 // k+1 and only then computes.  The pipelined march collides k-2 while the loads of k are
@@ -1533,6 +1750,62 @@ static cudaError_t launch_d3q19_tma(lbcg_ctx* c, const void* a, void* b)
     return cudaGetLastError();
 }
 
+// ----------------------------------------------------- psi-exchange march (host)
+static size_t xchg_smem(int wy) { return (8 * (size_t)(wy + 2) * 34 + 3 * 11 * 32 * (size_t)wy) * sizeof(float); }
+
+int xchg_resident_blocks(const lbcg_ctx* c)
+{
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    const int threads = 32 * c->block_rows;
+    cudaError_t e;
+    switch (c->p.precision) {
+        case LBCG_FP32:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_d3q19_xchg<LBCG_FP32>, threads,
+                                                              xchg_smem(c->block_rows));
+            break;
+        case LBCG_FP32_DEV:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_d3q19_xchg<LBCG_FP32_DEV>, threads,
+                                                              xchg_smem(c->block_rows));
+            break;
+        case LBCG_FP16_SCALED:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_d3q19_xchg<LBCG_FP16_SCALED>, threads,
+                                                              xchg_smem(c->block_rows));
+            break;
+        default: return 0;
+    }
+    return e == cudaSuccess ? per * sms : 0;
+}
+
+// Tables built and the progress bound met: more resident blocks than a tile's neighbours
+// span in list order (nsx + 2 columns) times the planes a tile can run ahead (rows + 2).
+bool xchg_supported(const lbcg_ctx* c)
+{
+    return c->d_xtiles && c->xntiles > 0 && c->xwy == c->block_rows && c->xrows == c->kp.rows &&
+           (long long)c->xgrid >= (long long)(c->xnsx + 2) * (c->xrows + 2) + 32 && small_index(c);
+}
+
+template <int PREC>
+static cudaError_t launch_d3q19_xchg(lbcg_ctx* c, const void* a, void* b)
+{
+    using S = typename Store<PREC>::S;
+    XParams X;
+    X.nsx = c->xnsx;
+    X.nsy = c->xnsy;
+    X.ntiles = c->xntiles;
+    X.rows = c->xrows;
+    X.tiles = c->d_xtiles;
+    X.map = c->d_xmap;
+    X.psi = c->d_psibuf;
+    X.flags = c->d_xflags;
+    X.ctl = c->d_xctl;
+    X.status = c->d_status;
+    k_step_d3q19_xchg<PREC><<<c->xgrid, dim3(32, c->block_rows), xchg_smem(c->block_rows), c->stream>>>(
+        c->kp, X, (const S*)a, (S*)b, c->d_link);
+    return cudaGetLastError();
+}
+
 template <int PREC, bool KEEP>
 static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant)
 {
@@ -1614,6 +1887,7 @@ int effective_variant(const lbcg_ctx* c)
     const bool reg = c->p.collision == LBCG_REG;
     int v = c->variant != 0 ? c->variant : (reg ? 6 : (prec == LBCG_FP64 ? 2 : 5));
     if (v == 8 && !tma_supported(c)) v = prec == LBCG_FP64 ? 6 : 7;
+    if (v == 10 && !xchg_supported(c)) v = 6;
     if ((v == 6 || v == 7) && !reg) v = prec == LBCG_FP64 ? 2 : 5;
     if (v == 4 && prec != LBCG_FP32 && prec != LBCG_FP32_DEV) v = 2;
     return v;
@@ -1633,6 +1907,11 @@ cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b)
         // default: 5 (re-read, three blocks per SM; measured fastest) for 4- and 2-byte storage;
         // FP64 re-reads with two blocks per SM (it spills at the three-block register budget)
         const int v = effective_variant(c);
+        if (v == 10) {
+            if (prec == LBCG_FP32) return launch_d3q19_xchg<LBCG_FP32>(c, a, b);
+            if (prec == LBCG_FP32_DEV) return launch_d3q19_xchg<LBCG_FP32_DEV>(c, a, b);
+            return launch_d3q19_xchg<LBCG_FP16_SCALED>(c, a, b);
+        }
         if (v == 8) {
             if (prec == LBCG_FP32) return launch_d3q19_tma<LBCG_FP32>(c, a, b);
             return launch_d3q19_tma<LBCG_FP32_DEV>(c, a, b);

@@ -133,7 +133,7 @@ def test_fp64_d3q19_step_emulsifier():
 # are held to rounding level.
 @pytest.mark.parametrize("rows,block_rows,variant", [(1, 3, 0), (5, 7, 0), (64, 8, 0), (5, 7, 1), (64, 8, 2), (3, 4, 4), (8, 8, 4),
                                                      (3, 5, 3), (8, 8, 3), (8, 8, 5), (3, 6, 5), (8, 8, 6), (3, 5, 6),
-                                                     (8, 8, 7), (5, 4, 7), (8, 8, 8), (3, 6, 8)])
+                                                     (8, 8, 7), (5, 4, 7), (8, 8, 8), (3, 6, 8), (8, 8, 10), (3, 5, 10)])
 def test_launch_shape_does_not_change_results(rows, block_rows, variant):
     lb = _lb()
     pb = W.step_emulsifier(nx=50, ny=30, nz=10, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10)
@@ -198,6 +198,54 @@ def test_tma_pipeline_timeout_is_reported(monkeypatch):
     good.step(10)
     ref.step(10)
     assert np.array_equal(good.populations(), ref.populations())
+
+
+# The psi-exchange march (variant 10) reads the ring psi that neighbour tiles publish
+# instead of pulling the ring sites; it computes what the register moment march (variant 6)
+# computes on walled and ported boxes closed in x and y, to rounding (the two kernels may
+# contract multiply-adds differently).
+@pytest.mark.parametrize("block_rows,rows", [(8, 8), (8, 4), (6, 3)])
+def test_psi_exchange_march_equals_moment_march(block_rows, rows):
+    lb = _lb()
+    probs = [W.step_emulsifier(nx=70, ny=30, nz=12, terrace_len=24, terrace_h=4, u_in=0.01, fill_x=12),
+             W.cross_junction_3d(nx=96, ny=40, nz=14),
+             W.static_droplet(W.D3Q19, 40, 9, ny=26, nz=18, centre=(19.5, 12.5, 8.5)).replace(periodic=(0, 0, 1))]
+    for prob in probs:
+        for prec in (lb.LBCG_FP32_DEV, lb.LBCG_FP32):
+            a = lb.Simulation(prob, prec, rows=rows, block_rows=block_rows, variant=6)
+            b = lb.Simulation(prob, prec, rows=rows, block_rows=block_rows, variant=10)
+            assert b.launch["variant"] == 10, (prob.name, b.launch)
+            a.step(45)
+            b.step(45)
+            d = np.abs(a.populations() - b.populations()).max()
+            assert d <= 1e-6, (prob.name, prec, d)
+
+
+def test_psi_exchange_unsupported_runs_moment_march():
+    lb = _lb()
+    s = lb.Simulation(W.static_droplet(W.D3Q19, 32, 8), lb.LBCG_FP32_DEV, variant=10)  # periodic in x and y
+    assert s.launch["variant"] == 6
+    s64 = lb.Simulation(W.step_emulsifier(nx=64, ny=30, nz=10, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10),
+                        lb.LBCG_FP64, variant=10)
+    assert s64.launch["variant"] == 6
+
+
+def test_psi_exchange_timeout_is_reported(monkeypatch):
+    lb = _lb()
+    prob = W.step_emulsifier(nx=64, ny=30, nz=10, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10)
+    monkeypatch.setenv("LBCG_TEST_PIPELINE_STALL", "1")
+    bad = lb.Simulation(prob, lb.LBCG_FP32_DEV, variant=10)
+    monkeypatch.delenv("LBCG_TEST_PIPELINE_STALL")
+    assert bad.launch["variant"] == 10
+    bad.step(1)
+    with pytest.raises(lb.LbcgError, match="timed out") as err:
+        bad.synchronize()
+    assert err.value.status == lb.LBCG_ERR_TIMEOUT
+    good = lb.Simulation(prob, lb.LBCG_FP32_DEV, variant=10)
+    ref = lb.Simulation(prob, lb.LBCG_FP32_DEV, variant=6)
+    good.step(10)
+    ref.step(10)
+    assert np.abs(good.populations() - ref.populations()).max() <= 1e-6
 
 
 def test_deterministic_repeat():
