@@ -16,6 +16,9 @@ f2  density ratio 1, 2, 5, 10 through alpha_k (D2Q9 128^2 R = 24, D3Q19 96^3 R =
     Laplace law against the unit-ratio sigma, spurious currents, mass drift, FP32-dev vs FP64.
 c2scan / c2drip  flow-focuser regime scans (pinch-off counts, d/h) over A, inlet speeds and
     viscosity ratio.
+c4  step emulsifier (768 x 128 x 32, FP32-dev, 2e5 steps, A = 0.1 and 0.3): detached droplets
+    beyond the terrace and their equivalent diameters; c4long: 1e6 steps at u_in 0.002 and
+    4e5 steps at u_in 0.005, both Ca = 0.01.
 f3  d/h against Q_B / (2 Q_Y) in the flow focuser (2e5 steps per case) and its fitted exponent
     (the paper reports 0.5, after Cubaud and Mason).
 """
@@ -194,6 +197,57 @@ def f3(steps: int = 200000) -> dict:
     return out
 
 
+def c4(steps: int = 200000, sample: int = 10000, cases=((0.1, 0.002), (0.3, 0.002))) -> list:
+    """Step emulsifier (Sec. IV B; 768 x 128 x 32, FP32-dev): the dispersed phase enters the
+    8-plane terrace at u_max 0.002 and breaks up where the terrace opens into the reservoir.
+    Droplets detached from the nozzle thread (red components lying entirely beyond the
+    terrace) are counted every `sample` steps; their equivalent diameters D = (6 V / pi)^(1/3)
+    are reported against the terrace height h = 8 and the nozzle width w = 126."""
+    rows = []
+    for A, u_in in cases:
+        pb = W.step_emulsifier(A=A, u_in=u_in)
+        sigma = 2 * A * pb.tau_b / 9
+        ca = (pb.tau_b - 0.5) / 3 * (2 * u_in / 3) / sigma
+        sim = lbcg.Simulation(pb, lbcg.LBCG_FP32_DEV)
+        t0 = time.perf_counter()
+        counts, diam = [], []
+        last = []
+        reach = 0
+        for t in range(sample, steps + 1, sample):
+            sim.step(sample)
+            labels, cnts, vols, nd = sim.label(cap=4096)
+            if nd == 0:
+                counts.append(0)
+                continue
+            lab = labels.reshape(pb.nz, pb.ny, pb.nx)
+            xs = np.broadcast_to(np.arange(pb.nx)[None, None, :], lab.shape)
+            roots = np.unique(lab[lab >= 0])
+            det = []
+            for k, r in enumerate(roots):
+                xr = xs[lab == r]
+                if xr.min() > 256:
+                    det.append((6.0 * vols[k] / math.pi) ** (1.0 / 3.0))
+                else:
+                    reach = max(reach, int(xr.max()))
+            counts.append(len(det))
+            diam += det
+            last = det
+        dt = time.perf_counter() - t0
+        o = sim.observables((384, 64, 16), allow_diverged=True)
+        rec = {"config": "C4 step emulsifier 768x128x32 FP32-dev", "A": A, "u_in": u_in, "Ca_estimate": ca,
+               "steps": steps, "thread_reach_x": reach,
+               "detached_max": max(counts) if counts else 0, "detached_final": len(last),
+               "D_mean": float(np.mean(diam)) if diam else None, "D_std": float(np.std(diam)) if diam else None,
+               "D_over_h": float(np.mean(diam)) / 8 if diam else None,
+               "D_over_w": float(np.mean(diam)) / 126 if diam else None,
+               "final_diameters": [round(float(d), 2) for d in sorted(last)], "nonfinite": o["nonfinite"],
+               "seconds": dt}
+        rows.append(rec)
+        print(json.dumps(rec), flush=True)
+        sim.close()
+    return rows
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", default="c1,c3,c2,f1")
@@ -226,6 +280,12 @@ def main(argv=None):
             res["f1"] = f1()
         elif name == "f2":
             res["f2"] = f2()
+        elif name == "c4":
+            res["c4"] = c4()
+        elif name == "c4long":
+            # Ca = 0.01 reached by A with the config's inlet speed over 10^6 steps, and by a
+            # faster inlet over 4 * 10^5 steps
+            res["c4long"] = c4(1000000, 50000, cases=((0.1, 0.002),)) + c4(400000, 20000, cases=((0.25, 0.005),))
         elif name == "f3":
             res["f3"] = f3(2 * args.c2_steps)
         elif name == "c2drip":
