@@ -18,7 +18,7 @@ c2scan / c2drip  flow-focuser regime scans (pinch-off counts, d/h) over A, inlet
     viscosity ratio.
 c4  step emulsifier (768 x 128 x 32, FP32-dev, 2e5 steps, A = 0.1 and 0.3): detached droplets
     beyond the terrace and their equivalent diameters; c4long: 1e6 steps at u_in 0.002 and
-    4e5 steps at u_in 0.005, both Ca = 0.01.
+    4e5 steps at u_in 0.005, both Ca = 0.01; c4nozzle: a single 24-wide nozzle, 4e5 steps.
 f3  d/h against Q_B / (2 Q_Y) in the flow focuser (2e5 steps per case) and its fitted exponent
     (the paper reports 0.5, after Cubaud and Mason).
 """
@@ -197,7 +197,7 @@ def f3(steps: int = 200000) -> dict:
     return out
 
 
-def c4(steps: int = 200000, sample: int = 10000, cases=((0.1, 0.002), (0.3, 0.002))) -> list:
+def c4(steps: int = 200000, sample: int = 10000, cases=((0.1, 0.002), (0.3, 0.002)), nozzle_w=None) -> list:
     """Step emulsifier (Sec. IV B; 768 x 128 x 32, FP32-dev): the dispersed phase enters the
     8-plane terrace at u_max 0.002 and breaks up where the terrace opens into the reservoir.
     Droplets detached from the nozzle thread (red components lying entirely beyond the
@@ -205,7 +205,7 @@ def c4(steps: int = 200000, sample: int = 10000, cases=((0.1, 0.002), (0.3, 0.00
     are reported against the terrace height h = 8 and the nozzle width w = 126."""
     rows = []
     for A, u_in in cases:
-        pb = W.step_emulsifier(A=A, u_in=u_in)
+        pb = W.step_emulsifier(A=A, u_in=u_in, nozzle_w=nozzle_w)
         sigma = 2 * A * pb.tau_b / 9
         ca = (pb.tau_b - 0.5) / 3 * (2 * u_in / 3) / sigma
         sim = lbcg.Simulation(pb, lbcg.LBCG_FP32_DEV)
@@ -234,7 +234,8 @@ def c4(steps: int = 200000, sample: int = 10000, cases=((0.1, 0.002), (0.3, 0.00
             last = det
         dt = time.perf_counter() - t0
         o = sim.observables((384, 64, 16), allow_diverged=True)
-        rec = {"config": "C4 step emulsifier 768x128x32 FP32-dev", "A": A, "u_in": u_in, "Ca_estimate": ca,
+        rec = {"config": "C4 step emulsifier 768x128x32 FP32-dev", "nozzle_w": nozzle_w or 126, "A": A,
+               "u_in": u_in, "Ca_estimate": ca,
                "steps": steps, "thread_reach_x": reach,
                "detached_max": max(counts) if counts else 0, "detached_final": len(last),
                "D_mean": float(np.mean(diam)) if diam else None, "D_std": float(np.std(diam)) if diam else None,
@@ -282,6 +283,9 @@ def main(argv=None):
             res["f2"] = f2()
         elif name == "c4":
             res["c4"] = c4()
+        elif name == "c4nozzle":
+            # a single 24-wide nozzle (w / h = 3): step emulsification, Ca 0.01-0.014
+            res["c4nozzle"] = c4(400000, 20000, cases=((0.25, 0.005), (0.18, 0.005)), nozzle_w=24)
         elif name == "c4long":
             # Ca = 0.01 reached by A with the config's inlet speed over 10^6 steps, and by a
             # faster inlet over 4 * 10^5 steps

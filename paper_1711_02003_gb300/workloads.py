@@ -268,19 +268,25 @@ def step_emulsifier(nx: int = 768, ny: int = 128, nz: int = 32, *, terrace_len: 
                     terrace_h: int = 8, u_in: float = 0.002, tau_cont: float = 1.0,
                     tau_disp: float = 1.0, A: float = 0.01, beta: float = 0.7,
                     outlet: int = PRESSURE_OUTLET, fill_x: int | None = None, seed: int = 0,
-                    roughness: int = 0) -> Problem:
+                    roughness: int = 0, nozzle_w: int | None = None) -> Problem:
     """3D step emulsifier ("volcano" nozzle, Sec. IV B, Fig. 5).
 
     Box nx x ny x nz.  Walls at y = 0, y = ny-1, z = 0 and z = nz-1.  Terrace for
     x < terrace_len: fluid z in [1, 1+terrace_h), solid above.  Reservoir for
     x >= terrace_len: full height.  Port 0: red (dispersed) velocity inlet at x = 0
     over the terrace cross-section; port 1: outlet at x = nx-1 over the reservoir.
-    `roughness` seeded single-site bumps are placed on the reservoir floor."""
+    `roughness` seeded single-site bumps are placed on the reservoir floor.  `nozzle_w`: the
+    terrace (and the inlet) only `nozzle_w` sites wide, centred in y (a single nozzle);
+    default the full channel width."""
     m = np.full((nz, ny, nx), WALL, dtype=np.uint8)
     zt = 1 + terrace_h
-    m[1:zt, 1:ny - 1, 1:terrace_len] = FLUID
+    ya, yb = 1, ny - 1
+    if nozzle_w is not None:
+        ya = max(1, (ny - nozzle_w) // 2)
+        yb = min(ny - 1, ya + nozzle_w)
+    m[1:zt, ya:yb, 1:terrace_len] = FLUID
     m[1:nz - 1, 1:ny - 1, terrace_len:nx - 1] = FLUID
-    m[1:zt, 1:ny - 1, 0] = PORT0 + 0
+    m[1:zt, ya:yb, 0] = PORT0 + 0
     m[1:nz - 1, 1:ny - 1, nx - 1] = PORT0 + 1
     if roughness:
         r = splitmix64(seed, 2 * roughness)
