@@ -674,6 +674,7 @@ int lbcg_init_fields_device(lbcg_ctx* c, const double* rr, const double* rb, con
 
 int lbcg_init_fields(lbcg_ctx* c, const double* rr, const double* rb, const double* u)
 {
+    const lbcg::TraceRange trace("lbcg_init_fields");
     int st = need(c, false);
     if (st) return st;
     if (!rr || !rb) return fail(LBCG_ERR_ARG, "null density field");
@@ -784,6 +785,7 @@ static int graph_for_current(lbcg_ctx* c, cudaGraphExec_t& exec)
 
 int lbcg_step(lbcg_ctx* c, long long nsteps)
 {
+    const lbcg::TraceRange trace("lbcg_step");
     int st = need(c, true);
     if (st) return st;
     if (nsteps < 0) return fail(LBCG_ERR_ARG, "negative step count");
@@ -849,6 +851,7 @@ int lbcg_get_fields_device(lbcg_ctx* c, double* rr, double* rb, double* u)
 
 int lbcg_get_fields(lbcg_ctx* c, double* rr, double* rb, double* u)
 {
+    const lbcg::TraceRange trace("lbcg_get_fields");
     int st = need(c, true);
     if (st) return st;
     if (!rr || !rb || !u) return fail(LBCG_ERR_ARG, "null output");
@@ -993,6 +996,7 @@ int lbcg_load(lbcg_ctx* c, const char* path)
 
 int lbcg_observables(lbcg_ctx* c, const double centre[3], double r_in, double r_out, lbcg_obs* out)
 {
+    const lbcg::TraceRange trace("lbcg_observables");
     int st = need(c, true);
     if (st) return st;
     if (!centre || !out) return fail(LBCG_ERR_ARG, "null centre or output");
@@ -1035,6 +1039,7 @@ int lbcg_observables_noalloc(const lbcg_params* p, const void* dev_state, const 
 
 int lbcg_label(lbcg_ctx* c, int32_t* labels, int64_t* counts, double* volumes, int cap, int* n_drops)
 {
+    const lbcg::TraceRange trace("lbcg_label");
     int st = need(c, true);
     if (st) return st;
     if (!labels || !n_drops || cap < 0) return fail(LBCG_ERR_ARG, "null output");

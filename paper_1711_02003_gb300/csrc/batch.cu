@@ -243,6 +243,7 @@ long long lbcg_batch_remaining(const lbcg_batch* b, int slot)
 
 int lbcg_batch_step(lbcg_batch* b, long long max_steps)
 {
+    const TraceRange trace("lbcg_batch_step");
     if (!b) return bfail(LBCG_ERR_ARG, "null batch");
     if (max_steps < 0) return bfail(LBCG_ERR_ARG, "negative step count");
     long long done = 0;

@@ -10,8 +10,17 @@
 #include <vector>
 
 #include "../../include/lbcg.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace lbcg {
+
+// NVTX range around a host entry point (visible to Nsight tools; inert otherwise)
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Per-site link word: bits 0..Q-1 = "pull along direction i bounces back" (the
 // upstream site x - c_i is a wall or outside a closed box face); bits 24..25 = site

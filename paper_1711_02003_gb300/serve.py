@@ -9,7 +9,10 @@ persistent fused kernel per lattice per step, replayed from a captured CUDA grap
 work from requests that arrived at different times overlaps on the GPU.  Finished
 requests are read back (observables), their memory is freed and waiting requests take
 their place.  The server reports time-to-result (finish - arrival) percentiles and the
-aggregate throughput.
+aggregate throughput.  A request withdrawn by its client (cancel_at) leaves the queue or is
+evicted from the device; with health checks on, a resident instance whose density went
+non-finite is evicted early; a finished one is reported diverged.  Neither disturbs the
+other requests.
 
 The scheduling logic talks to an Engine; :class:`LbcgEngine` runs the CUDA library, and
 tests substitute a host-only engine.
@@ -32,6 +35,7 @@ class Request:
     problem: W.Problem
     steps: int
     centre: tuple = None
+    cancel_at: float = None   # the client withdraws the request at this time (None: never)
 
 
 @dataclass
@@ -44,6 +48,7 @@ class Result:
     steps: int
     fluid_sites: int
     observables: dict = field(default_factory=dict)
+    status: str = "done"      # "done", "cancelled" (withdrawn), "diverged" (evicted)
 
     @property
     def time_to_result(self) -> float:
@@ -90,6 +95,14 @@ class Engine:
 
     def resident(self) -> int:
         raise NotImplementedError
+
+    def evict(self, handle) -> None:
+        """Remove an unfinished instance and free its memory (cancellation, divergence)."""
+        raise NotImplementedError
+
+    def diverged(self, handle) -> bool:
+        """Health check of a resident instance (only called when the server asks for checks)."""
+        return False
 
 
 class LbcgEngine(Engine):
@@ -144,14 +157,24 @@ class LbcgEngine(Engine):
     def resident(self) -> int:
         return len(self.handles)
 
+    def evict(self, handle) -> None:
+        sim, _ = self.handles.pop(handle)
+        self.batches[handle[0]].remove(handle[1])
+        sim.close()
+
+    def diverged(self, handle) -> bool:
+        sim, req = self.handles[handle]
+        return sim.observables(req.centre, allow_diverged=True)["nonfinite"] > 0
+
 
 class Server:
     """Continuous batching under an HBM budget (see the module docstring)."""
 
-    def __init__(self, engine: Engine, hbm_budget: float = 150e9, chunk: int = 100):
+    def __init__(self, engine: Engine, hbm_budget: float = 150e9, chunk: int = 100, health_every: int = 0):
         self.engine = engine
         self.budget = float(hbm_budget)
         self.chunk = int(chunk)
+        self.health_every = int(health_every)  # chunks between health checks of the residents (0: none)
         self.used = 0.0
         self.peak_used = 0.0
         self.peak_resident = 0
@@ -170,12 +193,35 @@ class Server:
 
         live = {}
         results = []
+        nchunks = 0
+
+        def drop(h, status):
+            r, need, t_adm = live.pop(h)
+            self.engine.evict(h)
+            self.used -= need
+            results.append(Result(r.rid, r.problem.lattice, r.arrival, t_adm, now(), r.steps,
+                                  r.problem.fluid_sites(), {}, status))
+
         while queue or live:
+            # withdrawn requests: dropped from the queue, evicted from the device
+            t = now()
+            for r in [r for r in queue if r.cancel_at is not None and r.cancel_at <= t]:
+                queue.remove(r)
+                results.append(Result(r.rid, r.problem.lattice, r.arrival, -1.0, t, r.steps,
+                                      r.problem.fluid_sites(), {}, "cancelled"))
+            for h in [h for h, (r, _, _) in live.items() if r.cancel_at is not None and r.cancel_at <= t]:
+                drop(h, "cancelled")
+            if self.health_every and nchunks and nchunks % self.health_every == 0:
+                for h in [h for h in live if self.engine.diverged(h)]:
+                    drop(h, "diverged")
+            if not queue and not live:
+                break
             # the resident requests advance asynchronously; the host admits meanwhile, so
             # instance set-up (allocation, geometry tables, initial state) overlaps GPU work
             advanced = bool(live)
             if advanced:
                 self.engine.advance(self.chunk)
+                nchunks += 1
                 if not realtime:
                     vclock += 1e-3
             # admission: arrived, fits the budget, free slot (first come, first served)
@@ -204,20 +250,25 @@ class Server:
                 r, need, t_adm = live.pop(h)
                 obs = self.engine.retire(h)
                 self.used -= need
+                status = "diverged" if obs.get("nonfinite", 0) > 0 else "done"
                 results.append(Result(r.rid, r.problem.lattice, r.arrival, t_adm, now(), r.steps,
-                                      r.problem.fluid_sites(), obs))
+                                      r.problem.fluid_sites(), obs, status))
         return sorted(results, key=lambda x: x.rid)
 
 
 def summary(results: list) -> dict:
-    """p50/p99 time-to-result and aggregate MLUPS (fluid-site updates / makespan)."""
-    if not results:
-        return {}
-    ttr = np.array([r.time_to_result for r in results])
+    """p50/p99 time-to-result and aggregate MLUPS (fluid-site updates / makespan) over the
+    completed requests; withdrawn and diverged requests are counted apart."""
+    done = [r for r in results if r.status == "done"]
+    if not done:
+        return {"requests": 0, "cancelled": len(results), "diverged": 0} if results else {}
+    ttr = np.array([r.time_to_result for r in done])
     start = min(r.arrival for r in results)
-    end = max(r.finished for r in results)
-    work = sum(r.fluid_sites * r.steps for r in results)
-    return {"requests": len(results), "p50_s": float(np.percentile(ttr, 50)), "p99_s": float(np.percentile(ttr, 99)),
+    end = max(r.finished for r in done)
+    work = sum(r.fluid_sites * r.steps for r in done)
+    return {"requests": len(done), "cancelled": sum(r.status == "cancelled" for r in results),
+            "diverged": sum(r.status == "diverged" for r in results),
+            "p50_s": float(np.percentile(ttr, 50)), "p99_s": float(np.percentile(ttr, 99)),
             "mean_s": float(ttr.mean()), "makespan_s": end - start, "site_updates": int(work),
             "aggregate_mlups": work / max(end - start, 1e-12) / 1e6}
 

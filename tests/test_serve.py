@@ -11,11 +11,15 @@ from paper_1711_02003_gb300 import workloads as W
 class FakeEngine(serve.Engine):
     """Instances advance `rate` steps per advance() call; bytes = 100 per site."""
 
-    def __init__(self, slots=3):
+    def __init__(self, slots=3, diverging=()):
         self.slots = slots
         self.live = {}
         self.order = []
         self.n = 0
+        self.evicted = []
+        self.diverging = set(diverging)  # request ids whose instance goes non-finite once it runs
+        self.bad = set()
+        self.steps_of = {}
 
     def state_bytes(self, req):
         return 100 * req.problem.nsites
@@ -27,6 +31,9 @@ class FakeEngine(serve.Engine):
         self.n += 1
         h = self.n
         self.live[h] = (req.problem.lattice, [req.steps])
+        self.steps_of[h] = req.steps
+        if req.rid in self.diverging:
+            self.bad.add(h)
         self.order.append(req.rid)
         return h
 
@@ -43,6 +50,13 @@ class FakeEngine(serve.Engine):
 
     def resident(self):
         return len(self.live)
+
+    def evict(self, h):
+        self.live.pop(h)
+        self.evicted.append(h)
+
+    def diverged(self, h):
+        return h in self.bad and self.live[h][1][0] < self.steps_of[h]
 
 
 def reqs(n=20, seed=3):
@@ -87,3 +101,35 @@ def test_make_requests_mix():
     assert lats == {W.D2Q9, W.D3Q19}
     assert all(r.steps >= 1 for r in rs)
     assert np.all(np.diff([r.arrival for r in rs]) > 0)
+
+
+# Failure paths, injected on the host: a client withdraws requests (before and after
+# admission) and an instance diverges; each is removed with its status, its memory is
+# returned to the budget, and every other request completes as before.
+def test_cancelled_requests_leave_queue_and_device():
+    rs = reqs(12)
+    budget = 3 * max(100 * r.problem.nsites for r in rs)
+    base = serve.Server(FakeEngine(slots=2), hbm_budget=budget, chunk=100).run(reqs(12), realtime=False)
+    rs[2].cancel_at = 0.0                       # withdrawn while still queued
+    rs[0].cancel_at = rs[0].arrival + 0.0005     # withdrawn after admission, before finishing
+    eng = FakeEngine(slots=2)
+    srv = serve.Server(eng, hbm_budget=budget, chunk=100)
+    res = {r.rid: r for r in srv.run(rs, realtime=False)}
+    assert res[2].status == "cancelled" and res[2].admitted < 0
+    assert res[0].status == "cancelled" and eng.evicted
+    assert srv.used == 0
+    assert all(res[r.rid].status == "done" for r in base if r.rid not in (0, 2))
+    s = serve.summary(list(res.values()))
+    assert s["cancelled"] == 2 and s["requests"] == len(rs) - 2
+
+
+def test_diverged_instance_evicted_without_disturbing_others():
+    rs = reqs(10)
+    budget = 3 * max(100 * r.problem.nsites for r in rs)
+    eng = FakeEngine(slots=2, diverging={4})
+    srv = serve.Server(eng, hbm_budget=budget, chunk=50, health_every=1)
+    res = {r.rid: r for r in srv.run(rs, realtime=False)}
+    assert res[4].status == "diverged"
+    assert all(res[k].status == "done" for k in res if k != 4)
+    assert len(res) == len(rs) and srv.used == 0
+    assert serve.summary(list(res.values()))["diverged"] == 1
