@@ -316,9 +316,11 @@ int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
  * environment variable LBCG_TEST_PIPELINE_STALL=1 is set makes every pipeline wait of
  * variants 8 and 10 run out (failure-path test): the step then leaves the state invalid and
  * lbcg_synchronize and the read-back calls report LBCG_ERR_TIMEOUT once.  The default is the
- * plain march for D2Q9; for D3Q19 with the regularized collision variant 6, with BGK
- * variant 5 (FP64: 2).  Within one variant results are bit-identical across
- * shapes; variants may contract multiply-adds and order sums differently and agree to
+ * moment march (6) for the regularized collision on either lattice; with BGK the plain
+ * march for D2Q9 and variant 5 (FP64: 2) for D3Q19.  D2Q9 takes 6 (moment march,
+ * regularized only), 3 (pipelined) and treats every other value as the plain march.
+ * Within one variant results are bit-identical across shapes; variants may contract
+ * multiply-adds and order sums differently and agree to
  * rounding.  Drops captured step graphs. */
 int lbcg_set_launch(lbcg_ctx* ctx, int rows, int block_rows, int variant);
 

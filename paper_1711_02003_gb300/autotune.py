@@ -7,8 +7,8 @@ scratch instance, and returns the fastest.  All candidates compute the same upda
 never changes results beyond rounding.
 
 Candidates:
-  D2Q9 : rows per warp strip in {2, 4, 8, 16, 32, 64} x variant {0 plain march, 3 pipelined}
-         (short strips give small boxes enough warps)
+  D2Q9 : rows per warp strip in {2, 4, 8, 16, 32, 64} x variant {6 moment march (regularized),
+         1 plain march, 3 pipelined} (short strips give small boxes enough warps)
   D3Q19: warps per block along y in {4, 6, 8} x z-planes per block in {4, 8, 16} x
          variant; regularized collision {7, 6 moment march (shared-memory / register
          moments), 5 re-read}, plus 12 and 16 warps per block for variant 7 and the
@@ -33,7 +33,8 @@ _CACHE = {}
 
 def candidates(lattice: int, precision: int, collision: int = 0) -> list:
     if lattice == lbcg.LBCG_D2Q9:
-        return [dict(rows=r, block_rows=0, variant=v) for v, r in itertools.product((0, 3), (2, 4, 8, 16, 32, 64))]
+        vs = (6, 1, 3) if collision == 0 else (1, 3)  # moment march (regularized only), plain, pipelined
+        return [dict(rows=r, block_rows=0, variant=v) for v, r in itertools.product(vs, (2, 4, 8, 16, 32, 64))]
     f64 = precision == lbcg.LBCG_FP64
     if collision == 0:  # regularized
         variants = [6, 7, 2] if f64 else [7, 6, 5]

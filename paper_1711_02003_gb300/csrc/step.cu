@@ -642,6 +642,109 @@ __global__ void __launch_bounds__(512, 2) k_step_d3q19_moms(const KParams P,
     tile_d3q19_mom<PREC, IDX, true>(P, A, B, link, bx, by, z0, z1, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
 }
 
+// ------------------------------------------------ D2Q9 moment march (2D variant 6)
+// strip_d2q9 with the waiting row held as the moments of the regularized collision (7 numbers
+// in 2D) instead of its 2Q populations; regularized collision only.
+template <int PREC, typename IDX>
+__device__ __forceinline__ void strip_d2q9_mom(const KParams& P, const typename Store<PREC>::S* __restrict__ A,
+                                               typename Store<PREC>::S* __restrict__ B,
+                                               const uint32_t* __restrict__ link, int sxi, int syi)
+{
+    using T = typename Store<PREC>::T;
+    using SP = Store<PREC>;
+    using L = Lat<0>;
+    constexpr int Q = 9;
+    const int lane = threadIdx.x & 31;
+    const int nx = P.nx, ny = P.ny;
+    const int x = sxi * 30 + lane - 1;
+    int xs;
+    const bool xok = wrap_coord(x, nx, P.per[0], xs) && x <= nx;
+    const bool xint = lane >= 1 && lane <= 30 && x < nx;
+    Up u;
+    nbr_off(xs, nx, P.per[0], u.xm, u.xp);
+    u.zm = u.zp = 0;
+    const int y0 = syi * P.rows;
+    const int y1 = min(y0 + P.rows, ny);
+    const IDX np = (IDX)P.np;
+    const Phys<T>& ph = phys<T>(P);
+    const T psi_wall = ph.psi_wall;
+
+    T psi_a = psi_wall, psi_b = psi_wall;  // rows yy-2, yy-1
+    SiteMom<T> mb;                         // moments of row yy-1
+    mom_zero(mb);
+    bool coll_b = false;
+    IDX s_b = 0;
+
+#pragma unroll 1
+    for (int yy = y0 - 1; yy <= y1; ++yy) {
+        int ys;
+        const bool yok = wrap_coord(yy, ny, P.per[1], ys);
+        int dym, dyp;
+        nbr_off(ys, ny, P.per[1], dym, dyp);
+        u.ym = (long long)dym * nx;
+        u.yp = (long long)dyp * nx;
+        SiteMom<T> mn;
+        mom_zero(mn);
+        T psi_n = psi_wall;
+        bool fluid_n = false;
+        const IDX s = (IDX)xs + (IDX)nx * (IDX)ys;
+        if (xok && yok) {
+            const uint32_t lk = link ? __ldg(link + s) : 0u;
+            const uint32_t type = (lk >> kTypeShift) & 3u;
+            if (type == kTypeFluid) {
+                psi_n = pull_moments<0, PREC, IDX, true>(P, A, s, u, lk, mn);
+                fluid_n = true;
+            } else if (type == kTypePort) {
+                psi_n = ghost_psi<0, PREC, IDX>(P, A, s);
+            }
+        }
+        if (yy - 1 >= y0) {  // warp-uniform: collide row yy-1
+            const T am = __shfl_up_sync(0xffffffffu, psi_a, 1), ap = __shfl_down_sync(0xffffffffu, psi_a, 1);
+            const T bm = __shfl_up_sync(0xffffffffu, psi_b, 1), bp = __shfl_down_sync(0xffffffffu, psi_b, 1);
+            const T nm = __shfl_up_sync(0xffffffffu, psi_n, 1), np_ = __shfl_down_sync(0xffffffffu, psi_n, 1);
+            if (coll_b) {
+                auto nb = [&](int cx, int cy) -> T {
+                    return cy < 0 ? (cx < 0 ? am : (cx > 0 ? ap : psi_a))
+                         : cy > 0 ? (cx < 0 ? nm : (cx > 0 ? np_ : psi_n))
+                                  : (cx < 0 ? bm : (cx > 0 ? bp : psi_b));
+                };
+                T F[3] = {T(0), T(0), T(0)};
+#pragma unroll
+                for (int k = 0; k < L::NP; ++k) {
+                    const int p = L::rep(k);
+                    const int cx = L::cx(p), cy = L::cy(p);
+                    const T d = (T)L::w(p) * (nb(cx, cy) - nb(-cx, -cy));
+                    if (cx) F[0] += cx > 0 ? d : -d;
+                    if (cy) F[1] += cy > 0 ? d : -d;
+                }
+                F[0] *= T(3);
+                F[1] *= T(3);
+                collide_moments<0, T>(ph, mb, F, [&](int i, T r, T g) {
+                    const IDX ir = (IDX)i * np + s_b;
+                    SP::store(B, ir, ir + (IDX)Q * np, ph, L::cls(i), r, g);
+                });
+            }
+        }
+        psi_a = psi_b;
+        psi_b = psi_n;
+        coll_b = fluid_n && xint && yy >= y0 && yy < y1;
+        s_b = s;
+        mb = mn;
+    }
+}
+
+template <int PREC, typename IDX>
+__global__ void __launch_bounds__(256) k_step_d2q9_mom(const KParams P, const typename Store<PREC>::S* __restrict__ A,
+                                                       typename Store<PREC>::S* __restrict__ B,
+                                                       const uint32_t* __restrict__ link,
+                                                       const int* __restrict__ tiles)
+{
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int sxi, syi;
+    if (!strip_of(P, tiles, gw, sxi, syi)) return;  // warp-uniform
+    strip_d2q9_mom<PREC, IDX>(P, A, B, link, sxi, syi);
+}
+
 // ------------------------------------------- TMA-staged moment march (variant 8)
 // The moment march of tile_d3q19_mom with its pulls served from shared memory.  For every
 // pulled plane, warp 0 of the block asks the tensor memory accelerator for Q boxes, one
@@ -1657,6 +1760,13 @@ static cudaError_t launch_d2q9(lbcg_ctx* c, const void* a, void* b)
     const int threads = 256;
     const long long blocks = (warps * 32 + threads - 1) / threads;
     const uint32_t* lk = c->any_link ? c->d_link : nullptr;
+    if (effective_variant(c) == 6) {
+        if (small_index(c))
+            k_step_d2q9_mom<PREC, int><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+        else
+            k_step_d2q9_mom<PREC, long long><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+        return cudaGetLastError();
+    }
     if (c->variant == 3) {
         if (small_index(c))
             k_step_d2q9_pipe<PREC, int><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
@@ -1881,7 +1991,12 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant
 int effective_variant(const lbcg_ctx* c)
 {
     const int prec = c->p.precision;
-    if (c->p.lattice == LBCG_D2Q9) return c->variant == 3 ? 3 : 0;
+    // D2Q9: 3 the pipelined march; the moment march (6) by default for the regularized
+    // collision (measured fastest on large boxes); every other value the plain march
+    if (c->p.lattice == LBCG_D2Q9) {
+        if (c->variant == 3) return 3;
+        return (c->variant == 0 || c->variant == 6) && c->p.collision == LBCG_REG ? 6 : 0;
+    }
     // default (measured fastest): the moment march with its moments in registers; the BGK
     // update needs the individual populations and re-reads them (three blocks per SM, FP64 two)
     const bool reg = c->p.collision == LBCG_REG;
