@@ -472,6 +472,10 @@ def main():
         "clocks": clocks,
         "cpu_baseline": cpu,
         "error_vs_f64_oracle": err,
+        "accuracy_gate": None if err is None else {
+            "fields_rel_tol": 1e-5, "passed": bool(err["rho_r"] <= 1e-5 and err["rho_b"] <= 1e-5),
+            "note": "FP32 gate of the component densities against the FP64 oracle (max-norm relative); "
+                    "FP16-scaled storage is reported and fails it by design"},
         "serving": serving,
         "observables": {"mass_r": obs["mass_r"], "mass_b": obs["mass_b"], "umax": obs["umax"],
                         "nonfinite": obs["nonfinite"]},
