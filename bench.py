@@ -217,7 +217,24 @@ def cpu_suite() -> dict:
             rows.append({"workload": name, "threads": nt, "steps": n, "seconds": dt,
                          "MLUPS": pb.fluid_sites() * n / dt / 1e6})
     oracle.set_threads(allt)
-    return {"cpu_suite": rows, "host": {"machine": platform.machine(), "cpus": os.cpu_count()}, "kind": "oracle"}
+    return {"cpu_suite": rows, "host": {"machine": platform.machine(), "cpus": os.cpu_count(), "model": cpu_model()},
+            "kind": "oracle"}
+
+
+def cpu_model() -> str:
+    """The host CPU's model line from /proc/cpuinfo (x86: model name; Arm: implementer and part)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read().splitlines()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model name"):
+        for line in info:
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    impl = next((ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU implementer")), "?")
+    part = next((ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU part")), "?")
+    return f"implementer {impl} part {part}"
 
 
 def error_vs_oracle(sim, osim) -> dict:
