@@ -19,6 +19,7 @@ c2scan / c2drip  flow-focuser regime scans (pinch-off counts, d/h) over A, inlet
 c4  step emulsifier (768 x 128 x 32, FP32-dev, 2e5 steps, A = 0.1 and 0.3): detached droplets
     beyond the terrace and their equivalent diameters; c4long: 1e6 steps at u_in 0.002 and
     4e5 steps at u_in 0.005, both Ca = 0.01; c4nozzle: a single 24-wide nozzle, 4e5 steps.
+c2prec  two dripping flow-focuser cases in FP32-dev and FP64 (pinch-offs, d/h), 2e5 steps each.
 f3  d/h against Q_B / (2 Q_Y) in the flow focuser (2e5 steps per case) and its fitted exponent
     (the paper reports 0.5, after Cubaud and Mason).
 """
@@ -76,10 +77,10 @@ def c3(steps: int = 5000) -> list:
 
 
 def c2(steps: int = 100000, sample: int = 500, A: float = 0.05, u: float = 0.005, tau_disp: float = 2.0,
-       u_cont: float | None = None) -> dict:
+       u_cont: float | None = None, precision: int = lbcg.LBCG_FP32_DEV) -> dict:
     u_cont = u if u_cont is None else u_cont
     pb = W.cross_junction(u_disp=u, u_cont=u_cont, A=A, tau_disp=tau_disp)
-    sim = lbcg.Simulation(pb, lbcg.LBCG_FP32_DEV)
+    sim = lbcg.Simulation(pb, precision)
     nx = pb.nx
     h = 64.0  # main channel width
     side_end = 320
@@ -118,7 +119,8 @@ def c2(steps: int = 100000, sample: int = 500, A: float = 0.05, u: float = 0.005
             diam.append(2.0 * math.sqrt(v / math.pi) / h)
     dt = time.perf_counter() - t0
     o = sim.observables((nx / 2, pb.ny / 2), allow_diverged=True)
-    return {"config": "C2 flow focuser D2Q9 1024x192 FP32-dev", "steps": steps, "A": A, "u_max": u,
+    return {"config": "C2 flow focuser D2Q9 1024x192 " + lbcg.PRECISION_NAMES[precision], "steps": steps, "A": A,
+            "u_max": u,
             "u_max_continuous": u_cont, "q_b_over_2q_y": u / (2 * u_cont),
             "thread_reach_x_mean": float(np.mean(thread)) if thread else None,
             "tau_disp": tau_disp, "tau_cont": pb.tau_b,
@@ -290,6 +292,14 @@ def main(argv=None):
             # Ca = 0.01 reached by A with the config's inlet speed over 10^6 steps, and by a
             # faster inlet over 4 * 10^5 steps
             res["c4long"] = c4(1000000, 50000, cases=((0.1, 0.002),)) + c4(400000, 20000, cases=((0.25, 0.005),))
+        elif name == "c2prec":
+            # the same dripping cases in FP32-dev and FP64: pinch-off counts and droplet sizes
+            res["c2prec"] = []
+            for A, ud in ((0.1, 0.003), (0.2, 0.004)):
+                for prec in (lbcg.LBCG_FP32_DEV, lbcg.LBCG_FP64):
+                    r = c2(2 * args.c2_steps, A=A, u=ud, tau_disp=2.0, u_cont=0.01, precision=prec)
+                    res["c2prec"].append(r)
+                    print(json.dumps(r), flush=True)
         elif name == "f3":
             res["f3"] = f3(2 * args.c2_steps)
         elif name == "c2drip":
