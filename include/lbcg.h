@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define LBCG_ABI_VERSION 1
+#define LBCG_ABI_VERSION 2
 #define LBCG_MAX_PORTS 8
 
 enum lbcg_status {
@@ -63,7 +63,8 @@ enum lbcg_status {
     LBCG_ERR_GEOMETRY = -6,  /* invalid mask / port table */
     LBCG_ERR_CAPACITY = -7,  /* caller buffer too small */
     LBCG_ERR_UNSUPPORTED = -8,
-    LBCG_ERR_TIMEOUT = -9      /* a bounded device-side wait or iteration ran out (state invalid) */
+    LBCG_ERR_TIMEOUT = -9,     /* a bounded device-side wait or iteration ran out (state invalid) */
+    LBCG_ERR_BOUNDS = -10      /* bounds-checked build: a step kernel met an index outside its array */
 };
 
 enum lbcg_lattice { LBCG_D2Q9 = 0, LBCG_D3Q19 = 1 };
@@ -145,6 +146,11 @@ const char* lbcg_strerror(int status);
 const char* lbcg_last_error(void);
 /* LBCG_ABI_VERSION of the loaded library. */
 int lbcg_abi_version(void);
+/* 1 if the loaded library is the bounds-checked debug build (compiled with
+ * -DLBCG_CHECK_BOUNDS: every population, link-word and psi-ring index of the step kernels
+ * is checked, an index outside its array is skipped and reported as LBCG_ERR_BOUNDS by
+ * lbcg_synchronize and the read-backs), 0 for the normal build.  Not part of the method. */
+int lbcg_bounds_checked(void);
 
 /* Bytes of ONE population buffer for these parameters (0 if they are invalid).
  * Layout: 2*Q planes of npad values of the storage type, npad = nsites rounded up to
@@ -196,6 +202,12 @@ int lbcg_set_populations(lbcg_ctx* ctx, const double* host_f);
 int lbcg_get_state(lbcg_ctx* ctx, void* host, size_t bytes);
 int lbcg_set_state(lbcg_ctx* ctx, const void* host, size_t bytes);
 
+/* The bound device buffer that holds the current (post-collision) state, in the layout of
+ * lbcg_state_bytes; the two bound buffers swap roles as steps run, so the answer is valid
+ * until the next lbcg_step.  NULL without a context or bound buffers.  Not part of the
+ * method; the paper has no counterpart. */
+void* lbcg_current_state(lbcg_ctx* ctx);
+
 /* Checkpoint file of the stored state: parameters, step count and raw state.  lbcg_load
  * requires the same lattice, box and precision (LBCG_ERR_ARG otherwise), restores the
  * step count and writes both buffers.  Synchronous. */
@@ -209,33 +221,33 @@ int lbcg_load(lbcg_ctx* ctx, const char* path);
 int lbcg_observables(lbcg_ctx* ctx, const double centre[3], double r_in, double r_out, lbcg_obs* out);
 
 /* Allocation-free observables.  The paper has no counterpart: this entry point exists
- * for callers that cannot allocate device memory, e.g. code recording a CUDA graph by
- * stream capture (cudaMalloc cannot be captured), plug-ins whose host application
- * owns every device allocation through its own pool, or loops that forbid allocation
- * after start-up.  It needs no context and allocates nothing: the caller passes the
- * inputs and receives the result; the reduction's scratch is a file-scope device
- * array of 131,328 bytes (1024 partial rows of 16 doubles plus 2 result rows) that
- * every GPU loading the library holds until the process exits.
+ * for callers that cannot allocate device memory, e.g. plug-ins whose host application
+ * owns every device allocation through its own pool, loops that forbid allocation after
+ * start-up, or code running with the device memory budget fully committed.  It needs no
+ * context and allocates nothing: the caller passes the inputs and receives the result;
+ * the reduction's scratch is a file-scope device array of 131,328 bytes (1024 partial
+ * rows of 16 doubles plus 2 result rows) that every GPU loading the library holds until
+ * the process exits.
  *   p        lattice, box and storage precision of the state (validated as by
  *            lbcg_create; LBCG_ERR_ARG otherwise)
  *   dev_state device buffer holding one population state in the layout of
- *            lbcg_state_bytes(p) (e.g. the buffer of a context that holds its current
- *            state); read only
+ *            lbcg_state_bytes(p) (e.g. lbcg_current_state of a context); read only
  *   dev_mask device array of nsites mask codes (only code 0 = fluid is counted), or
  *            NULL when every site is fluid
  *   centre, r_in, r_out   as for lbcg_observables
  *   stream   CUDA stream of the kernels (NULL = legacy default); the call waits for it
  *   out      host result; out->step = -1 (no context)
- * Results equal those of lbcg_observables for the same state.  The reduction launches
- * at most 1024 blocks whatever the lattice size, so every lattice the library accepts
- * fits; a request needing more partial rows than the array holds is rejected with
- * LBCG_ERR_CAPACITY.  The first call on each device looks up the array's device
- * address with cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture.  All calls share the one array and it keeps the last
- * call's contents (every row a call reads is written by that call first): calls whose
- * GPU work overlaps, on different streams or host threads, race and must be ordered
- * by the caller.  Returns LBCG_ERR_DIVERGED (out filled) when a fluid site has a
- * non-finite or non-positive density. */
+ * Results equal those of lbcg_observables for the same state.  The reduction launches at
+ * most 1024 blocks, each striding over the sites, so every lattice the library accepts
+ * fits the array.  The call is synchronous (it copies the result to the host and waits),
+ * so it cannot be recorded into a CUDA graph: on a stream that is being captured it
+ * returns LBCG_ERR_STATE without touching the stream.  The first call on each device looks
+ * up the array's device address with cudaGetSymbolAddress (with that device current).
+ * All calls share the one array and it keeps the last call's contents (every row a call
+ * reads is written by that call first): calls whose GPU work overlaps, on different
+ * streams or host threads, race and must be ordered by the caller.  Returns
+ * LBCG_ERR_DIVERGED (out filled) when a fluid site has a non-finite or non-positive
+ * density. */
 int lbcg_observables_noalloc(const lbcg_params* p, const void* dev_state, const uint8_t* dev_mask,
                              const double centre[3], double r_in, double r_out, void* stream, lbcg_obs* out);
 
@@ -274,6 +286,26 @@ long long lbcg_batch_remaining(const lbcg_batch* batch, int slot);
 int lbcg_batch_step(lbcg_batch* batch, long long max_steps);
 /* Wait for the batch's work, then report (once each) the slots that have no steps left. */
 int lbcg_batch_poll(lbcg_batch* batch, int* done_slots, int cap, int* ndone);
+
+/* Launch shape of a batch (0 in a field = default).  Not part of the method; the paper has
+ * no counterpart: it sets how the batched kernels cut the instances into work items and how
+ * many steps one captured graph replays, and is chosen by measurement (autotune.py).
+ *   rows             D2Q9: rows per warp strip (default 16); D3Q19: z-planes per tile (8)
+ *   block_rows       D3Q19: warps per block along y, 3..8 (8); 0 for D2Q9
+ *   strips_per_item  D2Q9: warp strips per work item (one block), 1..8 (8); 0 for D3Q19
+ *   blocks_per_sm    resident blocks per SM of the persistent grid (0 or more than fit: as
+ *                    many as fit, by the occupancy of the batched kernel on this device)
+ *   graph_steps      steps per captured graph, even, 2..256 (32)
+ *   sms              read back only: the device's SM count (grid = sms x blocks_per_sm)
+ * lbcg_batch_set_shape waits for the batch's stream, re-cuts every instance in the batch and
+ * drops the captured graph; results are bit-identical across shapes (the cut into work
+ * items changes nothing in the per-site arithmetic).
+ * lbcg_batch_get_shape returns the shape after defaults. */
+typedef struct {
+    int rows, block_rows, strips_per_item, blocks_per_sm, graph_steps, sms;
+} lbcg_batch_shape;
+int lbcg_batch_set_shape(lbcg_batch* batch, const lbcg_batch_shape* shape);
+int lbcg_batch_get_shape(const lbcg_batch* batch, lbcg_batch_shape* shape);
 /* Multiply-add throughput of the current device in GFLOP/s (2 flops per FMA), measured by
  * a kernel of independent FMA chains timed with CUDA events on `stream` (synchronises):
  * precision LBCG_FP64 for FP64, anything else for FP32.  The ALU roofline of the FP64 step
@@ -295,30 +327,27 @@ int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
 /* Launch shape of the fused step kernel (0 = library default):
  * rows: sites per warp along the marching axis (D2Q9: y rows per warp strip;
  * D3Q19: z planes per block); block_rows: D3Q19 warps per block along y (3..8; up to
- * 16 with variant 7 and the regularized collision);
+ * 16 with variant 7 and the regularized collision).
  * variant: 0 default, 1 keep the next row/plane's populations in registers,
- * 2 re-read them when colliding, 3 pipelined (collide row/plane k-2 while the loads
- * of k are in flight), 4 (D3Q19, 4-byte storage) asynchronous copies into a shared-
- * memory ring, 5 (D3Q19) re-read compiled for three resident blocks per SM,
- * 6 (D3Q19, regularized) moment march: the waiting plane is held as the 11 moments the
+ * 2 re-read them when colliding, 5 (D3Q19) re-read compiled for three resident blocks per
+ * SM, 6 (D3Q19, regularized) moment march: the waiting plane is held as the 11 moments the
  * regularized collision needs (Eq. 11 rebuilds every population from them), so nothing
  * is read twice, 7 the same with those moments in shared memory (64 registers),
  * 8 (D3Q19, regularized, FP32 or FP32-dev storage, nx a multiple of 4, block_rows 6 or
  * 8) the moment march with every plane's pulled populations staged in shared memory by
  * the tensor memory accelerator (two-stage pipeline of Q boxes per plane, bounded
- * waits); where its conditions do not hold it runs as 7 (FP64: 6).  10 (D3Q19,
- * regularized, 4- or 2-byte storage, box closed in x and y) psi-exchange march: tiles of
- * 32 x block_rows sites with no ring lanes or rows; each tile publishes psi of its planes
- * (per-site buffer and per-plane flags) and reads its x-y ring from its neighbour tiles
- * after bounded waits; persistent blocks take tiles in order; it runs as 6 where its
- * conditions or its forward-progress bound (enough resident blocks) do not hold.
- * Variants 6 and 7 fall back to 5 (FP64: 2) for the BGK collision.  A context created while the
- * environment variable LBCG_TEST_PIPELINE_STALL=1 is set makes every pipeline wait of
- * variants 8 and 10 run out (failure-path test): the step then leaves the state invalid and
+ * waits); where its conditions do not hold it runs as 7 (FP64: 6).  The D3Q19 moment
+ * marches (6, 7) refill the port ghosts of the state they write themselves (each block
+ * after its tile, from the populations it has just written), so a step with ports is one
+ * launch; the other variants run the separate refill kernel before each step.
+ * Variants 6 and 7 fall back to 5 (FP64: 2) for the BGK collision.  A context created while
+ * the environment variable LBCG_TEST_PIPELINE_STALL=1 is set makes every pipeline wait of
+ * variant 8 run out (failure-path test): the step then leaves the state invalid and
  * lbcg_synchronize and the read-back calls report LBCG_ERR_TIMEOUT once.  The default is the
  * moment march (6) for the regularized collision on either lattice; with BGK the plain
  * march for D2Q9 and variant 5 (FP64: 2) for D3Q19.  D2Q9 takes 6 (moment march,
- * regularized only), 3 (pipelined) and treats every other value as the plain march.
+ * regularized only) and treats every other value as the plain march.  Values 3, 4 and
+ * above 8 are rejected (LBCG_ERR_ARG).
  * Within one variant results are bit-identical across shapes; variants may contract
  * multiply-adds and order sums differently and agree to
  * rounding.  Drops captured step graphs. */
@@ -328,6 +357,12 @@ int lbcg_set_launch(lbcg_ctx* ctx, int rows, int block_rows, int variant);
  * the kernel variant actually run (never 0; see lbcg_set_launch).  Null outputs are
  * skipped. */
 int lbcg_get_launch(lbcg_ctx* ctx, int* rows, int* block_rows, int* variant);
+
+/* Grid of the next fused step launch: the number of thread blocks and threads per block,
+ * and the kernels one step launches (the fused step, plus the port refill unless the step
+ * kernel refills the port ghosts itself, as the D3Q19 moment marches do).  Not part of the
+ * method; the paper has no counterpart.  Null outputs are skipped. */
+int lbcg_get_grid(lbcg_ctx* ctx, long long* blocks, int* threads, int* kernels_per_step);
 
 #ifdef __cplusplus
 }

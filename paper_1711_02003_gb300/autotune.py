@@ -8,12 +8,15 @@ never changes results beyond rounding.
 
 Candidates:
   D2Q9 : rows per warp strip in {2, 4, 8, 16, 32, 64} x variant {6 moment march (regularized),
-         1 plain march, 3 pipelined} (short strips give small boxes enough warps)
+         1 plain march} (short strips give small boxes enough warps)
   D3Q19: warps per block along y in {4, 6, 8} x z-planes per block in {4, 8, 16} x
          variant; regularized collision {7, 6 moment march (shared-memory / register
          moments), 5 re-read}, plus 12 and 16 warps per block for variant 7 and the
          TMA-staged march (variant 8; 6 or 8 warps, 8 or 16 planes) for 4-byte storage; BGK
-         {5, 1, 2, 4 (4-byte storage only)}; FP64 regularized {6, 7, 2}, BGK {2, 1}
+         {5, 1, 2}; FP64 regularized {6, 7, 2}, BGK {2, 1}
+
+autotune_batch times the batched kernels' launch shapes (work-item cut, resident blocks per
+SM, steps per captured graph) on a set of instances, such as a sample of the serving mix.
 
 Run as a program it prints the candidate table of one named workload, in launch order
 (each candidate: `warm` untimed then `steps` timed launches of its step kernel):
@@ -33,13 +36,13 @@ _CACHE = {}
 
 def candidates(lattice: int, precision: int, collision: int = 0) -> list:
     if lattice == lbcg.LBCG_D2Q9:
-        vs = (6, 1, 3) if collision == 0 else (1, 3)  # moment march (regularized only), plain, pipelined
+        vs = (6, 1) if collision == 0 else (1,)  # moment march (regularized only), plain march
         return [dict(rows=r, block_rows=0, variant=v) for v, r in itertools.product(vs, (2, 4, 8, 16, 32, 64))]
     f64 = precision == lbcg.LBCG_FP64
     if collision == 0:  # regularized
         variants = [6, 7, 2] if f64 else [7, 6, 5]
     else:
-        variants = [2, 1] if f64 else [5, 1, 2] + ([4] if lbcg.ELEM_BYTES[precision] == 4 else [])
+        variants = [2, 1] if f64 else [5, 1, 2]
     out = [dict(rows=r, block_rows=b, variant=v) for v, b, r in itertools.product(variants, (4, 6, 8), (4, 8, 16))]
     if 7 in variants:
         out += [dict(rows=r, block_rows=b, variant=7) for b, r in itertools.product((12, 16), (4, 8))]
@@ -74,6 +77,58 @@ def autotune(pb, precision: int, steps: int = 30, cands: list | None = None, cac
     out = dict(best, table=table)
     if cache:
         _CACHE[key] = out
+    return out
+
+
+def batch_candidates(lattice: int) -> list:
+    """Batch launch shapes tried by autotune_batch (graph_steps is tuned after them)."""
+    if lattice == lbcg.LBCG_D2Q9:
+        return [dict(rows=r, strips_per_item=s, blocks_per_sm=b)
+                for r, s, b in itertools.product((8, 16, 32), (2, 4, 8), (0, 2))]
+    return [dict(rows=r, block_rows=w, blocks_per_sm=b) for w, r, b in itertools.product((4, 6, 8), (4, 8, 16), (0, 2))]
+
+
+def autotune_batch(problems: list, precision: int, steps: int = 64, cands: list | None = None,
+                   graph_steps=(16, 32, 64)) -> dict:
+    """Fastest batch launch shape for a set of instances of one lattice (e.g. a sample of the
+    serving mix): all of them go into one batch, each candidate shape times `steps` steps of
+    the whole batch (CUDA events on the batch's stream, after a warm-up that captures the
+    graph), then the steps per graph are tuned for the best shape.  Returns {'shape', 'mlups',
+    'table'}; aggregate MLUPS = fluid sites of all instances x steps / time."""
+    import torch
+    lattice = problems[0].lattice
+    stream = torch.cuda.Stream()
+    batch = lbcg.Batch(lattice, precision, len(problems), stream=stream)
+    sims = [lbcg.Simulation(pb, precision, stream=stream) for pb in problems]
+    for sim in sims:
+        batch.add(sim, 1 << 40)
+    fluid = sum(pb.fluid_sites() for pb in problems)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(shape):
+        batch.set_shape(**shape)
+        gs = batch.shape["graph_steps"]
+        batch.step(2 * gs)
+        stream.synchronize()
+        e0.record(stream)
+        batch.step(steps)
+        e1.record(stream)
+        stream.synchronize()
+        return fluid * steps / (e0.elapsed_time(e1) * 1e-3) / 1e6
+
+    table = [dict(c, mlups=timed(c)) for c in (cands or batch_candidates(lattice))]
+    best = max(table, key=lambda t: t["mlups"])
+    base = {k: v for k, v in best.items() if k != "mlups"}
+    for g in graph_steps:
+        table.append(dict(base, graph_steps=g, mlups=timed(dict(base, graph_steps=g))))
+    best = max(table, key=lambda t: t["mlups"])
+    batch.set_shape(**{k: v for k, v in best.items() if k != "mlups"})
+    out = {"shape": batch.shape, "mlups": best["mlups"], "instances": len(problems), "steps": steps, "table": table}
+    for slot in list(batch.sims):
+        batch.remove(slot)
+    for sim in sims:
+        sim.close()
+    batch.close()
     return out
 
 

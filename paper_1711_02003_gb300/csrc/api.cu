@@ -169,6 +169,7 @@ void fill_kparams(lbcg_ctx* c)
     if (c->p.lattice != LBCG_D2Q9 && c->block_rows <= 2) c->block_rows = 8;
     c->kp = make_kparams(c->p, c->dims, c->np, c->rows, c->block_rows);
     c->kp.stall_test = c->stall_test;
+    c->kp.status = c->d_status;
     c->kp.ntiles = c->d_tiles ? c->ntiles : 0;
 }
 
@@ -218,105 +219,53 @@ bool fitted_tiles_3d(const lbcg_ctx* c, const KParams& k, int ty, std::vector<in
     return true;
 }
 
-static void free_xchg(lbcg_ctx* c)
-{
-    cudaFree(c->d_xtiles);
-    cudaFree(c->d_xmap);
-    cudaFree(c->d_psibuf);
-    cudaFree(c->d_xflags);
-    cudaFree(c->d_xctl);
-    c->d_xtiles = c->d_xmap = c->d_xflags = c->d_xctl = nullptr;
-    c->d_psibuf = nullptr;
-    c->xntiles = c->xgrid = 0;
-}
-
-// Tiles of the psi-exchange march (variant 10, when asked for) for boxes closed in x and y
-// with the regularized collision in 4- or 2-byte storage: 32 x block_rows interior sites per tile,
-// uniform z-slabs of `rows` planes; a tile is listed when a fluid or port site lies in its
-// planes z0 - 1 .. z1 (its pulled planes), so every neighbour whose psi a listed tile reads
-// publishes it in the same step.  Order: slab, then column.
-static int build_xchg(lbcg_ctx* c)
-{
-    free_xchg(c);
-    const int prec = c->p.precision;
-    if (c->variant != 10 || c->p.lattice != LBCG_D3Q19 || c->p.collision != LBCG_REG || prec == LBCG_FP64 ||
-        c->p.periodic[0] || c->p.periodic[1] || !c->geometry || !c->any_link || c->block_rows > 8)
-        return LBCG_OK;  // built only when the psi-exchange march is asked for
-    const int nx = c->dims[0], ny = c->dims[1], nz = c->dims[2];
-    const int wy = c->block_rows, rows = c->kp.rows;
-    const int xnsx = (nx + 31) / 32, xnsy = (ny + wy - 1) / wy, xnsz = (nz + rows - 1) / rows;
-    const long long ncol = (long long)xnsx * xnsy;
-    std::vector<char> plane((size_t)(ncol * nz), 0);  // column has a fluid or port site in plane z
-    for (long long s = 0; s < c->n; ++s) {
-        const uint8_t m = c->mask[s];
-        if (m == LBCG_MASK_WALL) continue;
-        const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
-        plane[(size_t)(((x / 32) + (long long)xnsx * (y / wy)) * nz + z)] = 1;
-    }
-    std::vector<int> tiles, map((size_t)(ncol * xnsz), -1);
-    for (int sl = 0; sl < xnsz; ++sl) {
-        const int z0 = sl * rows, z1 = std::min(z0 + rows, nz);
-        for (long long col = 0; col < ncol; ++col) {
-            bool on = false;
-            for (int z = z0 - 1; z <= z1 && !on; ++z) {
-                int zs = z;
-                if (z < 0 || z >= nz) {
-                    if (!c->p.periodic[2]) continue;
-                    zs = z < 0 ? z + nz : z - nz;
-                }
-                on = plane[(size_t)(col * nz + zs)] != 0;
-            }
-            if (!on) continue;
-            map[(size_t)(sl * ncol + col)] = (int)(tiles.size() / 2);
-            tiles.push_back((int)col);
-            tiles.push_back(sl);
-        }
-    }
-    if (tiles.empty()) return LBCG_OK;
-    const int nt = (int)(tiles.size() / 2);
-    std::vector<float> psi((size_t)c->n, (float)c->p.psi_wall);
-    const int ctl[4] = {0, 0, 1, 0};
-    bool ok = cudaMalloc(&c->d_xtiles, sizeof(int) * tiles.size()) == cudaSuccess &&
-              cudaMalloc(&c->d_xmap, sizeof(int) * map.size()) == cudaSuccess &&
-              cudaMalloc(&c->d_psibuf, sizeof(float) * (size_t)c->n) == cudaSuccess &&
-              cudaMalloc(&c->d_xflags, sizeof(int) * (size_t)nt * (rows + 2)) == cudaSuccess &&
-              cudaMalloc(&c->d_xctl, sizeof(ctl)) == cudaSuccess;
-    if (!ok) {
-        free_xchg(c);
-        return fail(LBCG_ERR_NOMEM, "exchange tables allocation failed");
-    }
-    ok = cudaMemcpy(c->d_xtiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(c->d_xmap, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(c->d_psibuf, psi.data(), sizeof(float) * psi.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemset(c->d_xflags, 0, sizeof(int) * (size_t)nt * (rows + 2)) == cudaSuccess &&
-         cudaMemcpy(c->d_xctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice) == cudaSuccess;
-    if (!ok) {
-        free_xchg(c);
-        return fail(LBCG_ERR_CUDA, "exchange tables copy failed");
-    }
-    c->xnsx = xnsx;
-    c->xnsy = xnsy;
-    c->xnsz = xnsz;
-    c->xntiles = nt;
-    c->xrows = rows;
-    c->xwy = wy;
-    c->xgrid = xchg_resident_blocks(c);
-    return LBCG_OK;
-}
-
 static int build_active_tiles(lbcg_ctx* c);
 
 int build_tiles(lbcg_ctx* c)
 {
-    const int st = build_active_tiles(c);
-    if (st) return st;
-    return build_xchg(c);
+    return build_active_tiles(c);
+}
+
+// D3Q19 tiles of list `list` (column, z0 | z1 << 16): for every port ghost the tile that
+// collides its x', as per-tile row lists (gstart, grow) for the fused refill of the moment marches
+static int build_tile_ghosts(lbcg_ctx* c, const std::vector<int>& list)
+{
+    const KParams& k = c->kp;
+    const int nx = c->dims[0], ny = c->dims[1], ty = c->block_rows - 2;
+    const int nt = (int)(list.size() / 2);
+    std::vector<std::vector<int>> by_col((size_t)k.nsx * k.nsy);
+    for (int t = 0; t < nt; ++t) by_col[(size_t)list[2 * t]].push_back(t);
+    std::vector<int> owner((size_t)c->nghost, -1), count((size_t)nt + 1, 0);
+    for (int g = 0; g < c->nghost; ++g) {
+        const long long s = c->ghost_xp[(size_t)g];
+        const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
+        for (int t : by_col[(size_t)((x / 30) + (long long)k.nsx * (y / ty))]) {
+            const int z0 = list[2 * t + 1] & 0xffff, z1 = list[2 * t + 1] >> 16;
+            if (z >= z0 && z < z1) owner[(size_t)g] = t;
+        }
+        if (owner[(size_t)g] < 0) return fail(LBCG_ERR_GEOMETRY, "a port's inward neighbour lies in no tile");
+        ++count[(size_t)owner[(size_t)g] + 1];
+    }
+    for (int t = 0; t < nt; ++t) count[(size_t)t + 1] += count[(size_t)t];
+    std::vector<int> rows((size_t)std::max(c->nghost, 1)), fillp(count.begin(), count.end() - 1);
+    for (int g = 0; g < c->nghost; ++g) rows[(size_t)fillp[(size_t)owner[(size_t)g]]++] = g;
+    if (cudaMalloc(&c->d_gstart, sizeof(int) * count.size()) != cudaSuccess ||
+        cudaMalloc(&c->d_grow, sizeof(int) * rows.size()) != cudaSuccess)
+        return fail(LBCG_ERR_NOMEM, "tile ghost list allocation failed");
+    if (cudaMemcpy(c->d_gstart, count.data(), sizeof(int) * count.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_grow, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(LBCG_ERR_CUDA, "tile ghost list copy failed");
+    return LBCG_OK;
 }
 
 static int build_active_tiles(lbcg_ctx* c)
 {
     cudaFree(c->d_tiles);
+    cudaFree(c->d_gstart);
+    cudaFree(c->d_grow);
     c->d_tiles = nullptr;
+    c->d_gstart = nullptr;
+    c->d_grow = nullptr;
     c->ntiles = 0;
     c->kp.ntiles = 0;
     if (!c->geometry || !c->any_link) return LBCG_OK;
@@ -349,6 +298,7 @@ static int build_active_tiles(lbcg_ctx* c)
         return fail(LBCG_ERR_CUDA, "tile list copy failed");
     c->ntiles = (int)(c->p.lattice == LBCG_D2Q9 ? list.size() : list.size() / 2);
     c->kp.ntiles = c->ntiles;
+    if (c->p.lattice == LBCG_D3Q19 && c->nghost > 0) return build_tile_ghosts(c, list);
     return LBCG_OK;
 }
 
@@ -383,6 +333,7 @@ const char* lbcg_strerror(int s)
         case LBCG_ERR_CAPACITY: return "output capacity too small";
         case LBCG_ERR_UNSUPPORTED: return "unsupported";
         case LBCG_ERR_TIMEOUT: return "bounded wait or iteration ran out";
+        case LBCG_ERR_BOUNDS: return "index outside its array (bounds-checked build)";
         default: return "unknown status";
     }
 }
@@ -390,6 +341,15 @@ const char* lbcg_strerror(int s)
 const char* lbcg_last_error(void) { return g_err.c_str(); }
 
 int lbcg_abi_version(void) { return LBCG_ABI_VERSION; }
+
+int lbcg_bounds_checked(void)
+{
+#ifdef LBCG_CHECK_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 int lbcg_fma_peak(int precision, void* stream, double* gflops)
 {
@@ -451,11 +411,12 @@ void lbcg_destroy(lbcg_ctx* c)
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     free_tables(c);
     cudaFree(c->d_tiles);
+    cudaFree(c->d_gstart);
+    cudaFree(c->d_grow);
     cudaFree(c->d_scratch);
     cudaFree(c->d_partials);
     cudaFree(c->d_result);
     cudaFree(c->d_status);
-    free_xchg(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
@@ -471,6 +432,7 @@ int lbcg_bind_state(lbcg_ctx* c, void* a, void* b, size_t bytes)
     c->B = b;
     c->bound = true;
     c->fields = false;
+    c->ghosts_fresh = false;
     return LBCG_OK;
 }
 
@@ -616,10 +578,13 @@ int lbcg_set_geometry(lbcg_ctx* c, const uint8_t* mask, const lbcg_port* ports, 
     c->nports = nports;
     for (int m = 0; m < nports; ++m) c->ports[m] = ports[m];
     c->nghost = ng;
+    c->ghost_xp.assign(tab.begin() + ng, tab.begin() + 2 * ng);
     c->any_link = any;
     c->fluid_sites = fluid;
     c->geometry = true;
     c->fields = false;
+    c->ghosts_fresh = false;
+    fill_kparams(c);
     return build_tiles(c);
 }
 
@@ -646,6 +611,7 @@ static int scratch(lbcg_ctx* c, size_t bytes, void** out)
 // defined value at every site (walls stay zero, ghosts are refilled each step)
 static int mirror_state(lbcg_ctx* c)
 {
+    c->ghosts_fresh = false;
     LBCG_CUDA(cudaMemcpyAsync(c->B, c->A, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream), "mirror state");
     return LBCG_OK;
 }
@@ -736,12 +702,30 @@ static void drop_graphs(lbcg_ctx* c)
     }
 }
 
-// enqueue one step (port refill, fused kernel) on c->stream and swap the buffers
+// port refill of A before a step, unless the step kernel that wrote A refilled the ghosts
+static int refill_ports(lbcg_ctx* c)
+{
+    if (c->nghost > 0 && !(c->ghosts_fresh && step_fuses_ports(c)))
+        LBCG_CUDA(launch_fill_ports(c, c->A), "port fill kernel");
+    c->ghosts_fresh = true;
+    return LBCG_OK;
+}
+
+// after a step kernel: its output buffer becomes A; its ghosts are refilled only if the
+// kernel refills ports itself
+static void finish_step(lbcg_ctx* c)
+{
+    std::swap(c->A, c->B);
+    c->ghosts_fresh = step_fuses_ports(c);
+}
+
+// enqueue one step (port refill unless fused, fused kernel) on c->stream, swap the buffers
 static int one_step(lbcg_ctx* c)
 {
-    if (c->nghost > 0) LBCG_CUDA(launch_fill_ports(c, c->A), "port fill kernel");
+    const int st = refill_ports(c);
+    if (st) return st;
     LBCG_CUDA(launch_step(c, c->A, c->B), "step kernel");
-    std::swap(c->A, c->B);
+    finish_step(c);
     return LBCG_OK;
 }
 
@@ -759,6 +743,7 @@ static int graph_for_current(lbcg_ctx* c, cudaGraphExec_t& exec)
     cudaStream_t user = c->stream;
     void* a0 = c->A;
     void* b0 = c->B;
+    const bool fresh0 = c->ghosts_fresh;
     c->stream = c->cap_stream;
     cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
     int st = LBCG_OK;
@@ -776,6 +761,7 @@ static int graph_for_current(lbcg_ctx* c, cudaGraphExec_t& exec)
     c->stream = user;
     c->A = a0;
     c->B = b0;
+    c->ghosts_fresh = fresh0;
     if (st) return st;
     if (e != cudaSuccess) return cuda_fail(e, "graph capture");
     c->graph_start[slot] = a0;
@@ -791,25 +777,32 @@ int lbcg_step(lbcg_ctx* c, long long nsteps)
     if (nsteps < 0) return fail(LBCG_ERR_ARG, "negative step count");
     long long left = nsteps;
     if (left >= kGraphSteps) {
+        // a graph of fused steps starts from refilled ghosts: refill once before it if needed
+        if (step_fuses_ports(c) && !c->ghosts_fresh) {
+            st = refill_ports(c);
+            if (st) return st;
+        }
         while (left >= kGraphSteps) {
             cudaGraphExec_t exec = nullptr;
             st = graph_for_current(c, exec);
             if (st) return st;
             LBCG_CUDA(cudaGraphLaunch(exec, c->stream), "graph launch");
+            c->ghosts_fresh = step_fuses_ports(c);
             c->step += kGraphSteps;
             left -= kGraphSteps;
         }
     }
     for (; left > 0; --left) {
         if (c->timing) {
-            if (c->nghost > 0) LBCG_CUDA(launch_fill_ports(c, c->A), "port fill kernel");
+            st = refill_ports(c);
+            if (st) return st;
             cudaEvent_t e0, e1;
             st = next_events(c, e0, e1);
             if (st) return st;
             LBCG_CUDA(cudaEventRecord(e0, c->stream), "event record");
             LBCG_CUDA(launch_step(c, c->A, c->B), "step kernel");
             LBCG_CUDA(cudaEventRecord(e1, c->stream), "event record");
-            std::swap(c->A, c->B);
+            finish_step(c);
         } else {
             st = one_step(c);
             if (st) return st;
@@ -830,6 +823,8 @@ static int check_status(lbcg_ctx* c)
     LBCG_CUDA(cudaMemcpy(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
     if (h == 0) return LBCG_OK;
     LBCG_CUDA(cudaMemset(c->d_status, 0, sizeof(int)), "status reset");
+    if (h == kStatusBounds)
+        return fail(LBCG_ERR_BOUNDS, "step kernel: an index outside its array (bounds-checked build); the state is invalid");
     return fail(LBCG_ERR_TIMEOUT, "step kernel: a bounded wait timed out; the state is invalid");
 }
 
@@ -924,6 +919,8 @@ int lbcg_get_state(lbcg_ctx* c, void* host, size_t bytes)
     if (const int st_ = check_status(c)) return st_;
     return LBCG_OK;
 }
+
+void* lbcg_current_state(lbcg_ctx* c) { return c && c->bound ? c->A : nullptr; }
 
 int lbcg_set_state(lbcg_ctx* c, const void* host, size_t bytes)
 {
@@ -1121,6 +1118,26 @@ int lbcg_get_launch(lbcg_ctx* c, int* rows, int* block_rows, int* variant)
     return LBCG_OK;
 }
 
+int lbcg_get_grid(lbcg_ctx* c, long long* blocks, int* threads, int* kernels_per_step)
+{
+    if (!c) return fail(LBCG_ERR_ARG, "null context");
+    const KParams& k = c->kp;
+    long long b = 0;
+    int t = 0;
+    if (c->p.lattice == LBCG_D2Q9) {
+        const long long warps = c->d_tiles ? (long long)k.ntiles : (long long)k.nsx * k.nsy;
+        t = 256;
+        b = (warps * 32 + t - 1) / t;
+    } else {
+        t = 32 * c->block_rows;
+        b = c->d_tiles ? (long long)k.ntiles : (long long)k.nsx * k.nsy * k.nsz;
+    }
+    if (blocks) *blocks = b;
+    if (threads) *threads = t;
+    if (kernels_per_step) *kernels_per_step = 1 + (c->nghost > 0 && !step_fuses_ports(c) ? 1 : 0);
+    return LBCG_OK;
+}
+
 int lbcg_set_launch(lbcg_ctx* c, int rows, int block_rows, int variant)
 {
     if (!c) return fail(LBCG_ERR_ARG, "null context");
@@ -1128,9 +1145,9 @@ int lbcg_set_launch(lbcg_ctx* c, int rows, int block_rows, int variant)
     // blocks of up to 512 threads; every other kernel up to 256
     const int max_wy = variant == 7 && c->p.collision == LBCG_REG ? 16 : 8;
     if (rows < 0 || block_rows < 0 || (block_rows > 0 && (block_rows < 3 || block_rows > max_wy)) || variant < 0 ||
-        variant > 10 || variant == 9)
+        variant > 8 || variant == 3 || variant == 4)
         return fail(LBCG_ERR_ARG,
-                    "launch shape out of range (block_rows in 3..8, 3..16 with variant 7; variant in 0..8, 10)");
+                    "launch shape out of range (block_rows in 3..8, 3..16 with variant 7; variant in 0..2, 5..8)");
     c->rows = rows;
     c->block_rows = block_rows;
     c->variant = variant;

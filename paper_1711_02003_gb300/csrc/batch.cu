@@ -1,7 +1,7 @@
 // batch.cu -- many independent instances advanced together (lbcg_batch_*).
 //
 // A batch holds up to max_instances contexts of one lattice and storage precision.  Each
-// lbcg_batch_step chunk replays one captured CUDA graph of kBatchGraphSteps nodes; node k
+// lbcg_batch_step chunk replays one captured CUDA graph of graph_steps nodes; node k
 // refills the port ghosts and runs the batched fused step for every instance with more
 // than k steps left in the chunk.  Which instances take part, their buffers and step
 // counts live in a device table the host rewrites before each replay, so admitting or
@@ -17,8 +17,10 @@
 using namespace lbcg;
 
 namespace {
-constexpr int kBatchGraphSteps = 32;
-constexpr int kBatch2DRows = 16;
+constexpr int kBatchGraphSteps = 32;   // default steps per captured graph
+constexpr int kBatch2DRows = 16;       // default rows per D2Q9 warp strip
+constexpr int kBatch3DRows = 8;        // default z-planes per D3Q19 tile
+constexpr int kBatchStrips = 8;        // default D2Q9 strips (warps) per work item
 }  // namespace
 
 struct lbcg_batch {
@@ -42,6 +44,8 @@ struct lbcg_batch {
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t done[2] = {nullptr, nullptr};  // last replay that read table 0 / 1
     long long nrep = 0;                   // replays launched
+    lbcg_batch_shape shape{};             // launch shape after defaults (lbcg_batch_set_shape)
+    int grid = 0;                         // persistent grid: SMs x resident blocks per SM
 };
 
 namespace {
@@ -69,8 +73,8 @@ int rebuild(lbcg_batch* b)
         if (!b->ctx[s]) continue;
         const KParams& k = b->kp[s];
         if (b->lattice == LBCG_D2Q9) {
-            const int strips = k.nsx * k.nsy;
-            for (int f = 0; f < strips; f += 8) b->h_items.push_back({s, f, std::min(8, strips - f), 0});
+            const int strips = k.nsx * k.nsy, per = b->shape.strips_per_item;
+            for (int f = 0; f < strips; f += per) b->h_items.push_back({s, f, std::min(per, strips - f), 0});
         } else {
             // the instance's block tiles that hold fluid, with fitted z-ranges (computed at add)
             const std::vector<int>& tiles = b->tiles[s];
@@ -116,11 +120,12 @@ int capture(lbcg_batch* b)
     cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bfail(LBCG_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
     cudaError_t le = cudaSuccess;
-    for (int k = 0; k < kBatchGraphSteps && le == cudaSuccess; ++k) {
+    for (int k = 0; k < b->shape.graph_steps && le == cudaSuccess; ++k) {
         le = launch_batch_fill(b->lattice, b->precision, b->d_slots, b->d_fill, b->d_counts + 1, b->fill_cap, k,
                                b->cap_stream);
         if (le == cudaSuccess)
-            le = launch_batch_step(b->lattice, b->precision, b->d_slots, b->d_items, b->d_counts, k, b->cap_stream);
+            le = launch_batch_step(b->lattice, b->precision, b->d_slots, b->d_items, b->d_counts, k, b->grid,
+                                   b->shape.block_rows, b->cap_stream);
     }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->cap_stream, &g);
@@ -131,6 +136,43 @@ int capture(lbcg_batch* b)
     e = cudaGraphInstantiate(&b->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return bfail(LBCG_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    return LBCG_OK;
+}
+
+// shape after defaults; grid of the persistent kernel from the device's SM count
+int apply_shape(lbcg_batch* b, const lbcg_batch_shape& in)
+{
+    lbcg_batch_shape sh = in;
+    const bool d2 = b->lattice == LBCG_D2Q9;
+    if (sh.rows <= 0) sh.rows = d2 ? kBatch2DRows : kBatch3DRows;
+    sh.block_rows = d2 ? 0 : (sh.block_rows <= 0 ? 8 : sh.block_rows);
+    sh.strips_per_item = d2 ? (sh.strips_per_item <= 0 ? kBatchStrips : sh.strips_per_item) : 0;
+    if (sh.graph_steps <= 0) sh.graph_steps = kBatchGraphSteps;
+    if (sh.rows > 65535 || (!d2 && (sh.block_rows < 3 || sh.block_rows > 8)) ||
+        (d2 && (sh.strips_per_item < 1 || sh.strips_per_item > 8)) || sh.graph_steps < 2 || sh.graph_steps > 256 ||
+        (sh.graph_steps & 1) || sh.blocks_per_sm < 0 || sh.blocks_per_sm > 32)
+        return bfail(LBCG_ERR_ARG, "batch shape out of range (block_rows 3..8, strips_per_item 1..8, even "
+                                   "graph_steps 2..256, blocks_per_sm 0..32)");
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bfail(LBCG_ERR_CUDA, "SM count query failed");
+    const int fit = batch_resident_blocks(b->lattice, b->precision, d2 ? 8 : sh.block_rows);
+    if (fit <= 0) return bfail(LBCG_ERR_CUDA, "occupancy query of the batched kernel failed");
+    sh.blocks_per_sm = sh.blocks_per_sm <= 0 ? fit : std::min(sh.blocks_per_sm, fit);
+    sh.sms = sms;
+    b->shape = sh;
+    b->grid = sms * sh.blocks_per_sm;
+    return LBCG_OK;
+}
+
+// launch-shaped parameters and D3Q19 fitted tiles of slot s under the batch's shape
+int shape_slot(lbcg_batch* b, int s)
+{
+    lbcg_ctx* c = b->ctx[s];
+    b->kp[s] = make_kparams(c->p, c->dims, c->np, b->shape.rows, b->lattice == LBCG_D2Q9 ? 8 : b->shape.block_rows);
+    b->tiles[s].clear();
+    if (b->lattice != LBCG_D2Q9 && !fitted_tiles_3d(c, b->kp[s], b->shape.block_rows - 2, b->tiles[s]))
+        return bfail(LBCG_ERR_CAPACITY, "instance with nz above 65535 in a batch");
     return LBCG_OK;
 }
 
@@ -171,7 +213,40 @@ int lbcg_batch_create(int lattice, int precision, int max_instances, void* strea
     std::memset(b->h_slots, 0, 2 * sizeof(BatchSlot) * max_instances);
     cudaMemsetAsync(b->d_slots, 0, sizeof(BatchSlot) * max_instances, b->stream);
     cudaMemsetAsync(b->d_counts, 0, 2 * sizeof(int), b->stream);
+    const int st = apply_shape(b, lbcg_batch_shape{});
+    if (st) {
+        lbcg_batch_destroy(b);
+        return st;
+    }
     *out = b;
+    return LBCG_OK;
+}
+
+int lbcg_batch_set_shape(lbcg_batch* b, const lbcg_batch_shape* shape)
+{
+    if (!b || !shape) return bfail(LBCG_ERR_ARG, "null argument");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(LBCG_ERR_CUDA, cudaGetErrorString(e));
+    const lbcg_batch_shape old = b->shape;
+    int st = apply_shape(b, *shape);
+    if (st) return st;
+    for (int s = 0; s < b->max_slots; ++s) {
+        if (!b->ctx[s]) continue;
+        st = shape_slot(b, s);
+        if (st) {
+            b->shape = old;  // (the slot keeps its former parameters)
+            return st;
+        }
+    }
+    drop_graph(b);
+    b->dirty = true;
+    return LBCG_OK;
+}
+
+int lbcg_batch_get_shape(const lbcg_batch* b, lbcg_batch_shape* shape)
+{
+    if (!b || !shape) return bfail(LBCG_ERR_ARG, "null argument");
+    *shape = b->shape;
     return LBCG_OK;
 }
 
@@ -212,12 +287,11 @@ int lbcg_batch_add(lbcg_batch* b, lbcg_ctx* c, long long steps, int* slot)
     b->ctx[s] = c;
     b->remaining[s] = steps;
     b->reported[s] = 0;
-    b->kp[s] = make_kparams(c->p, c->dims, c->np, b->lattice == LBCG_D2Q9 ? kBatch2DRows : 8, 8);
-    b->tiles[s].clear();
-    if (b->lattice != LBCG_D2Q9 && !fitted_tiles_3d(c, b->kp[s], 8 - 2, b->tiles[s])) {
+    const int st = shape_slot(b, s);
+    if (st) {
         b->ctx[s] = nullptr;
         b->remaining[s] = 0;
-        return bfail(LBCG_ERR_CAPACITY, "instance with nz above 65535 in a batch");
+        return st;
     }
     b->dirty = true;
     *slot = s;
@@ -265,7 +339,7 @@ int lbcg_batch_step(lbcg_batch* b, long long max_steps)
         BatchSlot* const tab = b->h_slots + (size_t)k * b->max_slots;
         cudaError_t e = cudaEventSynchronize(b->done[k]);
         if (e != cudaSuccess) return bfail(LBCG_ERR_CUDA, cudaGetErrorString(e));
-        const long long chunk = std::min<long long>(kBatchGraphSteps, max_steps - done);
+        const long long chunk = std::min<long long>(b->shape.graph_steps, max_steps - done);
         for (int s = 0; s < b->max_slots; ++s) {
             BatchSlot& h = tab[s];
             lbcg_ctx* c = b->ctx[s];
@@ -293,6 +367,7 @@ int lbcg_batch_step(lbcg_batch* b, long long max_steps)
             const int n = tab[s].steps;
             if (n & 1) std::swap(c->A, c->B);
             c->step += n;
+            c->ghosts_fresh = false;  // the batched steps refill ports before each step only
             b->remaining[s] -= n;
         }
         done += chunk;

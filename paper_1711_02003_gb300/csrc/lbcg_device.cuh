@@ -82,6 +82,33 @@ struct Lat<1> {  // D3Q19
     __host__ __device__ static constexpr int rep(int k) { return 2 * k + 1; }
 };
 
+// ---------------------------------------------------- bounds-checked debug build
+// Compiled with -DLBCG_CHECK_BOUNDS, every population, link-word and psi-ring index of the
+// step kernels is checked before the access: an index outside its array sets the context's
+// status word to kStatusBounds (lbcg_synchronize and the read-backs then report
+// LBCG_ERR_BOUNDS) and the access is skipped (a load reads 0), so a faulty index is reported
+// instead of faulting the GPU.  Without the flag the checks compile to nothing.
+constexpr int kStatusTimeout = 1, kStatusBounds = 2;
+
+__device__ __forceinline__ bool in_bounds(const KParams& P, long long i, long long n)
+{
+#ifdef LBCG_CHECK_BOUNDS
+    if (i < 0 || i >= n) {
+        if (P.status) atomicExch(P.status, kStatusBounds);
+        return false;
+    }
+#endif
+    (void)P;
+    (void)i;
+    (void)n;
+    return true;
+}
+
+// elements of one state buffer (2Q planes of np values)
+__device__ __forceinline__ long long state_elems(const KParams& P) { return (P.lattice ? 38LL : 18LL) * (long long)P.np; }
+// sites of the box (link words)
+__device__ __forceinline__ long long box_sites(const KParams& P) { return (long long)P.nx * P.ny * P.nz; }
+
 // ---------------------------------------------------------------- storage formats
 // In registers every format becomes (r_i, g_i): r_i = f^R_i (red population) and
 // g_i = f^R_i + f^B_i - w_i rho0 (total deviation).  The collision works on these.
@@ -164,6 +191,12 @@ struct Store<LBCG_FP16_SCALED> {
         r = __half2float(a[ir]) * wi + 0.5f * ph.wr0[c];
         g = __half2float(a[ig]) * (wi * ph.inv_scale_g);
     }
+    __device__ static __forceinline__ void decode(S fr, S fg, const Phys<T>& ph, int c, T& r, T& g)
+    {
+        const float wi = ph.w[c];
+        r = __half2float(fr) * wi + 0.5f * ph.wr0[c];
+        g = __half2float(fg) * (wi * ph.inv_scale_g);
+    }
     template <typename IDX>
     __device__ static __forceinline__ void store(S* __restrict__ b, IDX ir, IDX ig, const Phys<T>& ph, int c, T r,
                                                  T g)
@@ -173,6 +206,42 @@ struct Store<LBCG_FP16_SCALED> {
         b[ig] = __float2half_rn(g * (iw * ph.scale_g));
     }
 };
+
+// population access through the bounds checks (ir: red-plane element, ig: second-plane element)
+template <int PREC, typename IDX>
+__device__ __forceinline__ void load_pop(const KParams& P, const typename Store<PREC>::S* __restrict__ a, IDX ir,
+                                         IDX ig, const Phys<typename Store<PREC>::T>& ph, int c,
+                                         typename Store<PREC>::T& r, typename Store<PREC>::T& g)
+{
+#ifdef LBCG_CHECK_BOUNDS
+    const long long n = state_elems(P);
+    if (!in_bounds(P, (long long)ir, n) || !in_bounds(P, (long long)ig, n)) {
+        r = g = 0;
+        return;
+    }
+#endif
+    Store<PREC>::load(a, ir, ig, ph, c, r, g);
+}
+
+template <int PREC, typename IDX>
+__device__ __forceinline__ void store_pop(const KParams& P, typename Store<PREC>::S* __restrict__ b, IDX ir, IDX ig,
+                                          const Phys<typename Store<PREC>::T>& ph, int c, typename Store<PREC>::T r,
+                                          typename Store<PREC>::T g)
+{
+#ifdef LBCG_CHECK_BOUNDS
+    const long long n = state_elems(P);
+    if (!in_bounds(P, (long long)ir, n) || !in_bounds(P, (long long)ig, n)) return;
+#endif
+    Store<PREC>::store(b, ir, ig, ph, c, r, g);
+}
+
+// link word of site s (0 without a link table)
+template <typename IDX>
+__device__ __forceinline__ uint32_t load_link(const KParams& P, const uint32_t* __restrict__ link, IDX s)
+{
+    if (!link || !in_bounds(P, (long long)s, box_sites(P))) return 0u;
+    return __ldg(link + s);
+}
 
 // ------------------------------------------------------------------ the collision
 // One fluid site.  In: r[i], g[i] post-streaming (Eq. 1), the colour gradient F.
@@ -454,6 +523,85 @@ __device__ __forceinline__ void collide_moments(const Phys<T>& ph, const SiteMom
         rsum += rp + rq;
     }
     out(0, rhoR - rsum, g0);
+}
+
+// ------------------------------------------------------------ port ghost refill
+// Ghost g of port m, inward neighbour x' (a fluid site):
+//   velocity:      f^k = f^{k,eq}(chi^k rho', u_port) + chi^k (f(x') - f^eq(x'))
+//   pressure:      f^k = f^{k,eq}(rho_port rho'^k / rho', u') + f^k(x') - f^{k,eq}(x')
+//   zero-gradient: f^k = f^k(x')
+// One thread per ghost, in the storage format's compute type, on the register form
+// (r_i = f^R_i, g_i = f_i - w_i rho0): every quantity formed is a small deviation, so
+// FP32 keeps the precision of the stored populations.  With phi^k_i = w_i + dphi^k_i and
+// P_i(u) = 3 c.u + 4.5 (c.u)^2 - 1.5 u^2:
+//   f^eq_i - w_i rho0 = w_i (rho - rho0) + rho_R dphi^R_i + rho_B dphi^B_i + w_i rho P_i(u),
+//   f^{R,eq}_i(rho_R, u) = rho_R (phi^R_i + w_i P_i(u)),
+// and the pressure rule reduces to f^k_i(x') + (rho_port / rho' - 1) f^{k,eq}_i(x').
+template <int LAT, int PREC>
+__device__ __forceinline__ void fill_one(const KParams& P, typename Store<PREC>::S* __restrict__ a,
+                                         const int* __restrict__ tab, const double* __restrict__ gu, int ng, int t)
+{
+    using L = Lat<LAT>;
+    using SP = Store<PREC>;
+    using T = typename SP::T;
+    constexpr int Q = L::Q;
+    const Phys<T>& ph = phys<T>(P);
+    const size_t np = P.np;
+    const size_t g = (size_t)tab[t];
+    const size_t xp = (size_t)tab[ng + t];
+    const int kind = tab[3 * ng + t];
+    T r[Q], d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) SP::load(a, i * np + xp, (Q + i) * np + xp, ph, L::cls(i), r[i], d[i]);
+    if (kind == LBCG_PORT_ZERO_GRADIENT) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) SP::store(a, i * np + g, (Q + i) * np + g, ph, L::cls(i), r[i], d[i]);
+        return;
+    }
+    T rr = 0, dr = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        rr += r[i];
+        dr += d[i];
+        if (L::cx(i)) jx += L::cx(i) > 0 ? d[i] : -d[i];
+        if (L::cy(i)) jy += L::cy(i) > 0 ? d[i] : -d[i];
+        if (L::cz(i)) jz += L::cz(i) > 0 ? d[i] : -d[i];
+    }
+    const T rho = ph.rho0 + dr;
+    const T rb = rho - rr;
+    const T inv_rho = T(1) / rho;
+    const T ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+    const T usq = ux * ux + uy * uy + uz * uz;
+    if (kind == LBCG_PORT_VELOCITY) {
+        const T vx = (T)gu[t], vy = (T)gu[ng + t], vz = (T)gu[2 * ng + t];
+        const T psi = (T)gu[4 * ng + t];
+        const T xr = (T(1) + psi) * T(0.5), xb = (T(1) - psi) * T(0.5);
+        const T vsq = vx * vx + vy * vy + vz * vz;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int c = L::cls(i);
+            const T wi = (T)L::w(i);
+            const T cu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
+            const T cv = (T)L::cx(i) * vx + (T)L::cy(i) * vy + (T)L::cz(i) * vz;
+            const T pu = T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq;
+            const T pv = T(3) * cv + T(4.5) * cv * cv - T(1.5) * vsq;
+            const T neq = d[i] - (wi * dr + rr * ph.dphiR[c] + rb * ph.dphiB[c] + wi * rho * pu);
+            const T gr = xr * rho * (ph.phiR[c] + wi * pv) + xr * neq;
+            const T gd = wi * dr + xr * rho * ph.dphiR[c] + xb * rho * ph.dphiB[c] + wi * rho * pv + neq;
+            SP::store(a, i * np + g, (Q + i) * np + g, ph, c, gr, gd);
+        }
+    } else {
+        const T fac = (T)gu[3 * ng + t] * inv_rho - T(1);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int c = L::cls(i);
+            const T wi = (T)L::w(i);
+            const T cu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
+            const T pu = wi * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq);
+            const T er = rr * (ph.phiR[c] + pu), eb = rb * (ph.phiB[c] + pu);
+            SP::store(a, i * np + g, (Q + i) * np + g, ph, c, r[i] + fac * er, d[i] + fac * (er + eb));
+        }
+    }
 }
 
 }  // namespace lbcg

@@ -53,6 +53,7 @@ struct KParams {
     int nsx, nsy, nsz;      // strips / blocks per axis
     int ntiles;             // entries of the active-tile list (0: launch every tile)
     int stall_test;         // failure-path test: TMA pipeline waits cannot complete (short limit)
+    int* status;            // context status word (bounded-wait timeouts, bounds-checked build)
     Phys<float> pf;
     Phys<double> pd;
     double alpha_r, alpha_b;
@@ -119,9 +120,17 @@ struct lbcg_ctx {
     double* d_ghost_u = nullptr;       // [3][nghost] inlet velocity
     long long fluid_sites = 0;
 
-    // tiles of the current launch shape that hold at least one fluid site (walled boxes only)
+    // tiles of the current launch shape that hold at least one fluid site (walled boxes only);
+    // D3Q19 with ports: the ghost-table rows of each tile's x' sites, d_grow[d_gstart[t] ..
+    // d_gstart[t+1]-1] for tile t (refilled by the moment marches after the tile)
     int* d_tiles = nullptr;
     int ntiles = 0;
+    int* d_gstart = nullptr;
+    int* d_grow = nullptr;
+    std::vector<int> ghost_xp;         // inward neighbour x' of each ghost-table row (host copy)
+    // the port ghosts of state A already hold the refill from A (written by a step kernel
+    // that refills ports itself), so that kernel may run without a refill launch before it
+    bool ghosts_fresh = false;
 
     // read-back / labelling / staging scratch (allocated on first use, kept)
     void* d_scratch = nullptr;
@@ -155,18 +164,6 @@ struct lbcg_ctx {
     int* d_status = nullptr;
     int stall_test = 0;  // LBCG_TEST_PIPELINE_STALL set when the context was created
 
-    // psi-exchange step kernel (variant 10): tiles of 32 x block_rows interior sites in
-    // uniform z-slabs of `rows` planes that hold a fluid or port site, ordered by slab then
-    // column; map (slab, column) -> tile index or -1; per-site psi published by the tiles;
-    // per-tile, per-plane flags holding the step epoch; control words (tile counter, blocks
-    // done, epoch)
-    int* d_xtiles = nullptr;
-    int* d_xmap = nullptr;
-    float* d_psibuf = nullptr;
-    int* d_xflags = nullptr;
-    int* d_xctl = nullptr;
-    int xnsx = 0, xnsy = 0, xnsz = 0, xntiles = 0, xrows = 0, xwy = 0, xgrid = 0;
-
     lbcg::KParams kp;
 };
 
@@ -176,8 +173,7 @@ namespace lbcg {
 cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b);
 int effective_variant(const lbcg_ctx* c);  // the step kernel variant launch_step runs
 bool tma_supported(const lbcg_ctx* c);     // the TMA-staged variant applies to this context
-int xchg_resident_blocks(const lbcg_ctx* c);  // persistent grid of the psi-exchange march
-bool xchg_supported(const lbcg_ctx* c);       // the psi-exchange march applies (tables built, progress bound)
+bool step_fuses_ports(const lbcg_ctx* c);  // the step kernel refills the port ghosts itself
 // launchers (aux.cu)
 cudaError_t launch_fill_ports(lbcg_ctx* c, void* a);
 cudaError_t launch_init(lbcg_ctx* c, const double* rr, const double* rb, const double* u, void* a);
@@ -189,7 +185,8 @@ cudaError_t launch_observables(lbcg_ctx* c, const void* a, const double centre[3
 cudaError_t launch_label(lbcg_ctx* c, const void* a, int32_t* parent, double* half, int* d_flag);
 // batched launchers (step.cu, aux.cu): one graph node each
 cudaError_t launch_batch_step(int lattice, int precision, const BatchSlot* slots, const BatchItem* items,
-                              const int* nitems, int k, cudaStream_t st);
+                              const int* nitems, int k, int grid, int wy, cudaStream_t st);
+int batch_resident_blocks(int lattice, int precision, int wy);  // per SM, 0 if unknown
 cudaError_t launch_batch_fill(int lattice, int precision, const BatchSlot* slots, const BatchItem* items,
                               const int* nitems, int cap, int k, cudaStream_t st);
 

@@ -1,12 +1,14 @@
 // noalloc.cu -- allocation-free observables reduction (lbcg_observables_noalloc).
 //
 // For callers that must not allocate device memory themselves or through the
-// library: code that runs while a CUDA stream is being captured into a graph
-// (cudaMalloc is not a capturable operation), plug-ins whose host application owns
-// every device allocation through its own pool, and real-time loops that forbid
-// allocation after start-up.  It computes what lbcg_observables computes, from a
-// caller-owned state buffer and an optional caller-owned device mask, without a
-// context; its reduction scratch is the file-scope array below.
+// library: plug-ins whose host application owns every device allocation through its
+// own pool, real-time loops that forbid allocation after start-up, and code running
+// with the device memory budget fully committed.  It computes what lbcg_observables
+// computes, from a caller-owned state buffer and an optional caller-owned device mask,
+// without a context; its reduction scratch is the file-scope array below.  The call is
+// synchronous (it reads the result back to the host), so it cannot be recorded into a
+// CUDA graph: on a stream that is being captured it returns LBCG_ERR_STATE at once.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -63,16 +65,17 @@ int noalloc_observables(const lbcg_params* p, const void* state, const uint8_t* 
     c.np = (size_t)((c.n + 127) / 128 * 128);
     fill_kparams(&c);
     const cudaStream_t st = (cudaStream_t)stream_ptr;
-    long long b = (c.n + 255) / 256;
-    if (b > kNaRows) b = kNaRows;
-    if (b < 1) b = 1;
-    const int nb = (int)b;
-    if (nb > kNaRows) {
-        err = "lbcg_observables_noalloc: reduction needs more partial rows than the static scratch holds";
-        return LBCG_ERR_CAPACITY;
+    // a synchronous read-back would invalidate a capture: refuse before touching the stream
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        err = "lbcg_observables_noalloc: synchronous call on a stream that is being captured";
+        return LBCG_ERR_STATE;
     }
+    // one partial row per block; the grid strides over the sites, so every lattice fits
+    const int nb = (int)std::min<long long>(kNaRows, std::max<long long>(1, (c.n + 255) / 256));
     double* scratch = nullptr;
-    cudaError_t e = na_scratch(&scratch);
+    e = na_scratch(&scratch);
     if (e != cudaSuccess) {
         err = std::string("lbcg_observables_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
         return LBCG_ERR_CUDA;

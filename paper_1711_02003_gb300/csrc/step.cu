@@ -98,14 +98,14 @@ __device__ __forceinline__ typename Store<PREC>::T pull_fluid(const KParams& P,
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const IDX ir = (IDX)i * np + s + up_off<LAT, IDX>(u, i);
-            SP::load(A, ir, ir + (IDX)Q * np, ph, L::cls(i), r[i], g[i]);
+            load_pop<PREC, IDX>(P, A, ir, ir + (IDX)Q * np, ph, L::cls(i), r[i], g[i]);
         }
     } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const bool bounce = (lk >> i) & 1u;
             const IDX ir = bounce ? (IDX)L::opp(i) * np + s : (IDX)i * np + s + up_off<LAT, IDX>(u, i);
-            SP::load(A, ir, ir + (IDX)Q * np, ph, L::cls(i), r[i], g[i]);
+            load_pop<PREC, IDX>(P, A, ir, ir + (IDX)Q * np, ph, L::cls(i), r[i], g[i]);
         }
     }
     T rr = r[0], sg = g[0];
@@ -132,7 +132,7 @@ __device__ __forceinline__ typename Store<PREC>::T ghost_psi(const KParams& P,
     for (int i = 0; i < L::Q; ++i) {
         T r, g;
         const IDX ir = (IDX)i * np + s;
-        SP::load(A, ir, ir + (IDX)L::Q * np, phys<T>(P), L::cls(i), r, g);
+        load_pop<PREC, IDX>(P, A, ir, ir + (IDX)L::Q * np, phys<T>(P), L::cls(i), r, g);
         rr += r;
         sg += g;
     }
@@ -151,7 +151,7 @@ __device__ __forceinline__ void store_site(const KParams& P, typename Store<PREC
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         const IDX ir = (IDX)i * np + s;
-        Store<PREC>::store(B, ir, ir + (IDX)L::Q * np, phys<T>(P), L::cls(i), r[i], g[i]);
+        store_pop<PREC, IDX>(P, B, ir, ir + (IDX)L::Q * np, phys<T>(P), L::cls(i), r[i], g[i]);
     }
 }
 
@@ -190,6 +190,18 @@ __device__ __forceinline__ void block_of(const KParams& P, const int* __restrict
         z0 = (int)blockIdx.z * P.rows;
         z1 = min(z0 + P.rows, P.nz);
     }
+}
+
+// psi-ring access through the bounds checks (ring of 4 planes x the block's threads)
+template <typename T>
+__device__ __forceinline__ void ring_put(const KParams& P, T* ring, int i, T v)
+{
+    if (in_bounds(P, i, 4LL * blockDim.x * blockDim.y)) ring[i] = v;
+}
+template <typename T>
+__device__ __forceinline__ T ring_get(const KParams& P, const T* ring, int i)
+{
+    return in_bounds(P, i, 4LL * blockDim.x * blockDim.y) ? ring[i] : T(0);
 }
 
 // ------------------------------------------------------------------------ D2Q9
@@ -235,7 +247,7 @@ __device__ __forceinline__ void strip_d2q9(const KParams& P, const typename Stor
         bool fluid_n = false;
         const IDX s = (IDX)xs + (IDX)nx * (IDX)ys;
         if (xok && yok) {
-            const uint32_t lk = link ? __ldg(link + s) : 0u;
+            const uint32_t lk = load_link(P, link, s);
             const uint32_t type = (lk >> kTypeShift) & 3u;
             if (type == kTypeFluid) {
                 psi_n = pull_fluid<0, PREC, IDX>(P, A, s, u, lk, rn, gn);
@@ -347,7 +359,7 @@ __device__ __forceinline__ void tile_d3q19(const KParams& P, const typename Stor
         bool fluid_n = false;
         const IDX s = sxy + (IDX)nxy * (IDX)zs;
         if (xok && yok && zok) {
-            const uint32_t lk = link ? __ldg(link + s) : 0u;
+            const uint32_t lk = load_link(P, link, s);
             const uint32_t type = (lk >> kTypeShift) & 3u;
             if (type == kTypeFluid) {
                 psi_n = pull_fluid<1, PREC, IDX>(P, A, s, u, lk, rn, gn);
@@ -357,7 +369,7 @@ __device__ __forceinline__ void tile_d3q19(const KParams& P, const typename Stor
             }
         }
         const int slot_n = (zz - z0 + 1) & 3;
-        psi_s[(slot_n * WY + w) * 32 + lane] = psi_n;
+        ring_put(P, psi_s, (slot_n * WY + w) * 32 + lane, psi_n);
         __syncthreads();
         if (zz - 1 >= z0 && coll_b) {
             const int zc = zz - 1;
@@ -368,12 +380,12 @@ __device__ __forceinline__ void tile_d3q19(const KParams& P, const typename Stor
                 Up uc = u;
                 uc.zm = (long long)a * nxy;
                 uc.zp = (long long)b * nxy;
-                const uint32_t lk = link ? __ldg(link + sc) : 0u;
+                const uint32_t lk = load_link(P, link, sc);
                 pull_fluid<1, PREC, IDX>(P, A, sc, uc, lk, rb, gb);
             }
             auto nb = [&](int cx, int cy, int cz) -> T {
                 const int slot = (zc + cz - z0 + 1) & 3;
-                return psi_s[(slot * WY + (w + cy)) * 32 + (lane + cx)];
+                return ring_get(P, psi_s, (slot * WY + (w + cy)) * 32 + (lane + cx));
             };
             T F[3] = {T(0), T(0), T(0)};
 #pragma unroll
@@ -425,6 +437,34 @@ __global__ void __launch_bounds__(256, 3) k_step_d3q19_occ(const KParams P,
     int bx, by, z0, z1;
     block_of(P, tiles, bx, by, z0, z1);
     tile_d3q19<PREC, false, IDX>(P, A, B, link, bx, by, z0, z1, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+}
+
+// ------------------------------------------------------------ fused port refill
+// A step kernel that refills port ghosts itself: the host assigns every ghost to the block
+// tile that collides its inward neighbour x' (rows gstart[t] .. gstart[t+1]-1 of grow are the
+// ghost-table rows of tile t).  After its tile, a block holding such ghosts rebuilds them in
+// the output buffer from the populations of x' its threads have just written there (fill_one,
+// the rule of the separate refill, one thread per ghost), so the next step finds them
+// refilled without a refill launch.
+
+struct PortTab {
+    const int* tab;     // ghost table [4][ng] (site, inward neighbour, port, kind) or nullptr
+    const double* gu;   // [5][ng] inlet velocity, port density, port psi
+    int ng;
+    const int* gstart;  // [ntiles + 1] first row in grow of each tile
+    const int* grow;    // ghost-table rows grouped by tile
+};
+
+template <int PREC>
+__device__ __forceinline__ void refill_tile_ports(const KParams& P, typename Store<PREC>::S* B, const PortTab& pt,
+                                                  int tile)
+{
+    const int g0 = pt.gstart[tile], g1 = pt.gstart[tile + 1];
+    if (g0 >= g1) return;  // block-uniform
+    __syncthreads();       // the populations of every x' of the tile are written
+    const int nt = blockDim.x * blockDim.y;
+    for (int e = g0 + threadIdx.y * blockDim.x + threadIdx.x; e < g1; e += nt)
+        fill_one<1, PREC>(P, B, pt.tab, pt.gu, pt.ng, pt.grow[e]);
 }
 
 // ------------------------------------------------- moment march (variants 6, 7; regularized)
@@ -481,7 +521,7 @@ __device__ __forceinline__ typename Store<PREC>::T pull_moments(const KParams& P
         auto ld = [&](int i, T& r, T& g) {
             IDX ir = (IDX)i * np + s + up_off<LAT, IDX>(u, i);
             if (WALLS && ((lk >> i) & 1u)) ir = (IDX)L::opp(i) * np + s;
-            SP::load(A, ir, ir + (IDX)Q * np, ph, L::cls(i), r, g);
+            load_pop<PREC, IDX>(P, A, ir, ir + (IDX)Q * np, ph, L::cls(i), r, g);
         };
         T r0, g0;
         ld(0, r0, g0);
@@ -569,7 +609,7 @@ __device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename 
         const IDX s = sxy + (IDX)nxy * (IDX)zs;
         const bool full = row_in && zz >= z0 && zz < z1;  // block-uniform in z, warp-uniform in y
         if (xok && yok && zok) {
-            const uint32_t lk = link ? __ldg(link + s) : 0u;
+            const uint32_t lk = load_link(P, link, s);
             const uint32_t type = (lk >> kTypeShift) & 3u;
             if (type == kTypeFluid) {
                 psi_n = full ? pull_moments<1, PREC, IDX, true>(P, A, s, u, lk, mn)
@@ -580,7 +620,7 @@ __device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename 
             }
         }
         const int slot_n = (zz - z0 + 1) & 3;
-        psi_s[(slot_n * WY + w) * 32 + lane] = psi_n;
+        ring_put(P, psi_s, (slot_n * WY + w) * 32 + lane, psi_n);
         if (MSMEM && fluid_n && full) mom_put(mn, mom_s + (zz & 1) * 11 * mstride, mstride);
         __syncthreads();
         if (zz - 1 >= z0 && coll_b) {
@@ -588,7 +628,7 @@ __device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename 
             const IDX sc = sxy + (IDX)nxy * (IDX)zc;
             auto nb = [&](int cx, int cy, int cz) -> T {
                 const int slot = (zc + cz - z0 + 1) & 3;
-                return psi_s[(slot * WY + (w + cy)) * 32 + (lane + cx)];
+                return ring_get(P, psi_s, (slot * WY + (w + cy)) * 32 + (lane + cx));
             };
             T F[3] = {T(0), T(0), T(0)};
 #pragma unroll
@@ -606,7 +646,7 @@ __device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename 
             if (MSMEM) mom_get(mb, mom_s + (zc & 1) * 11 * mstride, mstride);
             collide_moments<1, T>(ph, mb, F, [&](int i, T r, T g) {
                 const IDX ir = (IDX)i * np + sc;
-                SP::store(B, ir, ir + (IDX)Q * np, ph, L::cls(i), r, g);
+                store_pop<PREC, IDX>(P, B, ir, ir + (IDX)Q * np, ph, L::cls(i), r, g);
             });
         }
         coll_b = fluid_n && inner && zz >= z0 && zz < z1;
@@ -614,32 +654,36 @@ __device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename 
     }
 }
 
-// variant 6: moments in registers; three blocks per SM (FP64: two, at 128 registers)
+// variant 6: moments in registers; three blocks per SM (FP64: two, at 128 registers).  With
+// per-tile ghost lists the kernel refills the port ghosts itself (refill_tile_ports).
 template <int PREC, typename IDX>
 __global__ void __launch_bounds__(256, PREC == LBCG_FP64 ? 2 : 3) k_step_d3q19_mom(const KParams P,
                                                            const typename Store<PREC>::S* __restrict__ A,
                                                            typename Store<PREC>::S* __restrict__ B,
-                                                           const uint32_t* __restrict__ link, const int* __restrict__ tiles)
+                                                           const uint32_t* __restrict__ link, const int* __restrict__ tiles,
+                                                           const PortTab pt)
 {
     extern __shared__ unsigned char smem_raw[];
     int bx, by, z0, z1;
     block_of(P, tiles, bx, by, z0, z1);
     tile_d3q19_mom<PREC, IDX, false>(P, A, B, link, bx, by, z0, z1, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+    if (pt.tab) refill_tile_ports<PREC>(P, B, pt, (int)blockIdx.x);
 }
 
 // variant 7: the moment march with the waiting moments in shared memory; 64 registers, so
-// four blocks of 8 warps or two of 16 per SM
+// four blocks of 8 warps or two of 16 per SM; refills port ghosts like variant 6
 template <int PREC, typename IDX>
 __global__ void __launch_bounds__(512, 2) k_step_d3q19_moms(const KParams P,
                                                                 const typename Store<PREC>::S* __restrict__ A,
                                                                 typename Store<PREC>::S* __restrict__ B,
                                                                 const uint32_t* __restrict__ link,
-                                                                const int* __restrict__ tiles)
+                                                                const int* __restrict__ tiles, const PortTab pt)
 {
     extern __shared__ unsigned char smem_raw[];
     int bx, by, z0, z1;
     block_of(P, tiles, bx, by, z0, z1);
     tile_d3q19_mom<PREC, IDX, true>(P, A, B, link, bx, by, z0, z1, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+    if (pt.tab) refill_tile_ports<PREC>(P, B, pt, (int)blockIdx.x);
 }
 
 // ------------------------------------------------ D2Q9 moment march (2D variant 6)
@@ -689,7 +733,7 @@ __device__ __forceinline__ void strip_d2q9_mom(const KParams& P, const typename 
         bool fluid_n = false;
         const IDX s = (IDX)xs + (IDX)nx * (IDX)ys;
         if (xok && yok) {
-            const uint32_t lk = link ? __ldg(link + s) : 0u;
+            const uint32_t lk = load_link(P, link, s);
             const uint32_t type = (lk >> kTypeShift) & 3u;
             if (type == kTypeFluid) {
                 psi_n = pull_moments<0, PREC, IDX, true>(P, A, s, u, lk, mn);
@@ -721,7 +765,7 @@ __device__ __forceinline__ void strip_d2q9_mom(const KParams& P, const typename 
                 F[1] *= T(3);
                 collide_moments<0, T>(ph, mb, F, [&](int i, T r, T g) {
                     const IDX ir = (IDX)i * np + s_b;
-                    SP::store(B, ir, ir + (IDX)Q * np, ph, L::cls(i), r, g);
+                    store_pop<PREC, IDX>(P, B, ir, ir + (IDX)Q * np, ph, L::cls(i), r, g);
                 });
             }
         }
@@ -802,6 +846,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0u;
 }
 
+// count `bytes` of the current phase's expected transaction bytes as arrived
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
 // bounded wait for the phase with the given parity to complete; false after `limit` polls
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit)
 {
@@ -825,7 +876,7 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
 template <int PREC, int WY, bool FULL>
 __device__ __forceinline__ float pull_staged(const KParams& P, const float* __restrict__ box,
                                              const typename Store<PREC>::S* __restrict__ A, int s, const Up& u,
-                                             uint32_t lk, bool edge, int x, int y, const int (&sh)[3],
+                                             uint32_t lk, bool edge, int x, int y, const int (&sh)[3], int boff,
                                              SiteMom<float>& m)
 {
     using L = Lat<1>;
@@ -844,12 +895,16 @@ __device__ __forceinline__ float pull_staged(const KParams& P, const float* __re
                                   (P.per[1] && (unsigned)(y - L::cy(i)) >= (unsigned)P.ny);
                 if (bounce || wrap) {
                     const int ir = bounce ? L::opp(i) * np + s : i * np + s + up_off<1, int>(u, i);
-                    SP::load(A, ir, ir + Q * np, ph, L::cls(i), r, g);
+                    load_pop<PREC, int>(P, A, ir, ir + Q * np, ph, L::cls(i), r, g);
                     return;
                 }
             }
-            const float* b = box + i * SF + sh[L::cx(i) + 1];
-            SP::decode(b[0], b[TmaLayout<WY>::ROWS], ph, L::cls(i), r, g);
+            const int o = i * SF + sh[L::cx(i) + 1];  // from the box start, which lies boff into the stage
+            if (!in_bounds(P, boff + o, SF * Q - TmaLayout<WY>::ROWS)) {
+                r = g = 0.f;
+                return;
+            }
+            SP::decode(box[o], box[o + TmaLayout<WY>::ROWS], ph, L::cls(i), r, g);
         };
         float r0, g0;
         ld(0, r0, g0);
@@ -966,23 +1021,36 @@ __device__ __forceinline__ void tile_d3q19_tma(const KParams& P, const CUtensorM
         const int s = sxy + nxy * zs;
         const bool full = row_in && zz >= z0 && zz < z1;
         if (got && xok && yok && zok) {
-            const uint32_t lk = link ? __ldg(link + s) : 0u;
+            const uint32_t lk = load_link(P, link, s);
             const uint32_t type = (lk >> kTypeShift) & 3u;
             if (type == kTypeFluid) {
                 const float* box = reinterpret_cast<const float*>(smem + stg * Lay::STAGE) + w * kTmaBoxX + lane;
-                psi_n = full ? pull_staged<PREC, WY, true>(P, box, A, s, u, lk, edge, x, y, sh, mn)
-                             : pull_staged<PREC, WY, false>(P, box, A, s, u, lk, edge, x, y, sh, mn);
+                const int boff = w * kTmaBoxX + lane;
+                psi_n = full ? pull_staged<PREC, WY, true>(P, box, A, s, u, lk, edge, x, y, sh, boff, mn)
+                             : pull_staged<PREC, WY, false>(P, box, A, s, u, lk, edge, x, y, sh, boff, mn);
                 fluid_n = true;
             } else if (type == kTypePort) {
                 psi_n = ghost_psi<1, PREC, int>(P, A, s);
             }
         }
-        psi_s[(((k & 3) * WY) + w) * 32 + lane] = psi_n;
+        ring_put(P, psi_s, (((k & 3) * WY) + w) * 32 + lane, psi_n);
         if (__syncthreads_or(!got)) {
-            // a copy did not arrive: record it, wait (bounded) for both stages, give up
-            if (lane == 0 && w == 0) atomicExch(status, 1);
-            mbar_wait(&bar[stg], (uint32_t)((k >> 1) & 1), wait_limit);
-            if (k + 1 < nplanes) mbar_wait(&bar[stg ^ 1], (uint32_t)(((k + 1) >> 1) & 1), wait_limit);
+            // a phase did not complete: record it, then wait (bounded) until the copies still
+            // in flight into this block's shared memory have landed before the block exits.
+            // In the failure-path test the phases of planes k and k + 1 (both outstanding)
+            // miss only the 16 extra bytes nobody sends: count those as arrived, so each phase
+            // completes exactly when its real copies have landed.  On a real timeout the
+            // missing bytes are unknown and the waits below just run out.
+            if (lane == 0 && w == 0) {
+                atomicExch(status, 1);
+                if (P.stall_test) {
+                    mbar_complete_tx(&bar[stg], extra_tx);
+                    if (k + 1 < nplanes) mbar_complete_tx(&bar[stg ^ 1], extra_tx);
+                }
+            }
+            __syncthreads();
+            mbar_wait(&bar[stg], (uint32_t)((k >> 1) & 1), kTmaWaitLimit);
+            if (k + 1 < nplanes) mbar_wait(&bar[stg ^ 1], (uint32_t)(((k + 1) >> 1) & 1), kTmaWaitLimit);
             return;
         }
         // every thread is done with stage stg: refill it with plane zz + 2
@@ -995,7 +1063,7 @@ __device__ __forceinline__ void tile_d3q19_tma(const KParams& P, const CUtensorM
             const int sc = sxy + nxy * zc;
             auto nb = [&](int cx, int cy, int cz) -> T {
                 const int slot = (k - 1 + cz) & 3;
-                return psi_s[(slot * WY + (w + cy)) * 32 + (lane + cx)];
+                return ring_get(P, psi_s, (slot * WY + (w + cy)) * 32 + (lane + cx));
             };
             T F[3] = {T(0), T(0), T(0)};
 #pragma unroll
@@ -1012,7 +1080,7 @@ __device__ __forceinline__ void tile_d3q19_tma(const KParams& P, const CUtensorM
             F[2] *= T(3);
             collide_moments<1, T>(ph, mb, F, [&](int i, T r, T g) {
                 const int ir = i * np + sc;
-                SP::store(B, ir, ir + Q * np, ph, L::cls(i), r, g);
+                store_pop<PREC, int>(P, B, ir, ir + Q * np, ph, L::cls(i), r, g);
             });
         }
         coll_b = fluid_n && inner && full;
@@ -1032,620 +1100,6 @@ __global__ void __launch_bounds__(32 * WY, WY <= 6 ? 3 : 2) k_step_d3q19_tma(con
     int bx, by, z0, z1;
     block_of(P, tiles, bx, by, z0, z1);
     tile_d3q19_tma<PREC, WY>(P, &tmA, A, B, link, bx, by, z0, z1, smem_tma, status);
-}
-
-// --------------------------------------- psi-exchange moment march (variant 10)
-// The psi ring of a block tile is the one quantity the tile cannot compute from its own
-// sites; the other marches recompute it by pulling the ring sites' 2Q populations (32 x WY
-// threads pull for 30 x (WY - 2) collided sites).  Here every thread owns an interior site
-// (tiles of 32 x WY) and the tiles exchange psi instead: after summing plane z a tile
-// publishes psi of its sites (per-site buffer, then its flag for that plane = the step's
-// epoch), waits for the flags of its eight x-y neighbour tiles for the same plane and
-// reads their edge psi from L2.  z-ring planes are still pulled (tiles of one x-y column
-// are in different slabs).  Blocks are persistent and take tiles in list order (slab, then
-// column); a tile is at most one plane ahead of its neighbours, so with more than
-// (nsx + 2)(rows + 2) resident blocks the oldest tile always completes (checked on the
-// host, else variant 6 runs).  Waits are bounded: on a timeout the status word is set,
-// every other wait gives up at once, the step completes with an invalid state and the host
-// reports LBCG_ERR_TIMEOUT.  The last block to finish resets the tile counter and advances
-// the epoch, so replays of a captured graph need no host involvement.  Regularized
-// collision, 4- and 2-byte storage, boxes closed in x and y.
-struct XParams {
-    int nsx, nsy, ntiles, rows;
-    const int* tiles;  // [ntiles][2]: column bx + nsx * by, slab
-    const int* map;    // [slab][column]: tile index or -1 (no fluid or port in its planes)
-    float* psi;        // per-site psi of the current step (psi_wall where never written)
-    int* flags;        // [ntiles][rows + 2]: epoch of the last publication of each plane
-    int* ctl;          // [0] next tile, [1] blocks done, [2] epoch
-    int* status;       // nonzero: a wait timed out (every later wait gives up)
-};
-
-constexpr int kXWaitLimit = 1 << 16;  // polls of a neighbour flag (32 ns sleeps) before giving up
-
-template <int PREC>
-__global__ void __launch_bounds__(256, 4) k_step_d3q19_xchg(const KParams P, const XParams X,
-                                                            const typename Store<PREC>::S* __restrict__ A,
-                                                            typename Store<PREC>::S* __restrict__ B,
-                                                            const uint32_t* __restrict__ link)
-{
-    using T = typename Store<PREC>::T;
-    using SP = Store<PREC>;
-    using L = Lat<1>;
-    constexpr int Q = 19;
-    extern __shared__ unsigned char smem_raw[];
-    T* const ring = reinterpret_cast<T*>(smem_raw);  // [8][WY + 2][34]
-    __shared__ int s_tile;
-    const int lane = threadIdx.x, w = threadIdx.y, WY = blockDim.y, tid = w * 32 + lane;
-    const int RW = 34, RH = WY + 2;
-    const int mstride = WY * 32;
-    T* const mom = ring + 8 * RH * RW + tid;  // [plane mod 3][11][WY * 32], thread-private
-    const int nx = P.nx, ny = P.ny, nz = P.nz;
-    const int nxy = nx * ny;
-    const int np = (int)P.np;
-    const Phys<T>& ph = phys<T>(P);
-    const T psi_wall = ph.psi_wall;
-    const int epoch = *(volatile const int*)(X.ctl + 2);
-    const int nplanes_max = X.rows + 2;
-
-    for (;;) {
-        if (tid == 0) s_tile = atomicAdd(X.ctl, 1);
-        __syncthreads();
-        const int t = s_tile;
-        __syncthreads();
-        if (t >= X.ntiles) break;
-        const int col = X.tiles[2 * t], slab = X.tiles[2 * t + 1];
-        const int bx = col % X.nsx, by = col / X.nsx;
-        const int x0 = bx * 32, y0 = by * WY;
-        const int x = x0 + lane, y = y0 + w;
-        const bool inb = x < nx && y < ny;
-        const int xs = inb ? x : 0, ys = inb ? y : 0;
-        Up u;
-        {
-            int a, b;
-            nbr_off(xs, nx, 0, u.xm, u.xp);
-            nbr_off(ys, ny, 0, a, b);
-            u.ym = (long long)a * nx;
-            u.yp = (long long)b * nx;
-        }
-        const int sxy = xs + nx * ys;
-        const int z0 = slab * X.rows, z1 = min(z0 + X.rows, nz);
-        const int nplanes = z1 - z0 + 2;
-        // waiter lanes 0..7 of the last warp: the eight x-y neighbour tiles of the same slab
-        int nbt = -1;
-        if (w == WY - 1 && lane < 8) {
-            const int dx = lane < 3 ? lane - 1 : (lane == 3 ? -1 : (lane == 4 ? 1 : lane - 6));
-            const int dy = lane < 3 ? -1 : (lane < 5 ? 0 : 1);
-            const int nbx = bx + dx, nby = by + dy;
-            if (nbx >= 0 && nbx < X.nsx && nby >= 0 && nby < X.nsy)
-                nbt = X.map[(size_t)slab * X.nsx * X.nsy + nbx + X.nsx * nby];
-        }
-
-        // iteration k pulls plane z0 - 1 + k, publishes it, collides plane z0 - 3 + k (its
-        // ring planes are complete) and only then waits for the neighbours' plane k and
-        // fetches its ring edge: one barrier per plane, the wait overlapping the collision
-        unsigned coll_bits = 0;  // bit k: plane z0 - 1 + k is collided by this thread
-#pragma unroll 1
-        for (int k = 0; k <= nplanes; ++k) {
-            const int zz = z0 - 1 + k;
-            const bool pulling = k < nplanes;
-            int zs = 0;
-            const bool zok = pulling && wrap_coord(zz, nz, P.per[2], zs);
-            const int slot = k & 7;
-            if (pulling) {
-                {
-                    int a, b;
-                    nbr_off(zs, nz, P.per[2], a, b);
-                    u.zm = (long long)a * nxy;
-                    u.zp = (long long)b * nxy;
-                }
-                SiteMom<T> mn;
-                mom_zero(mn);
-                T psi_n = psi_wall;
-                bool fluid_n = false;
-                const int site = sxy + nxy * zs;
-                const bool full = zz >= z0 && zz < z1;
-                if (inb && zok) {
-                    const uint32_t lk = __ldg(link + site);
-                    const uint32_t type = (lk >> kTypeShift) & 3u;
-                    if (type == kTypeFluid) {
-                        psi_n = full ? pull_moments<1, PREC, int, true>(P, A, site, u, lk, mn)
-                                     : pull_moments<1, PREC, int, false>(P, A, site, u, lk, mn);
-                        fluid_n = true;
-                    } else if (type == kTypePort) {
-                        psi_n = ghost_psi<1, PREC, int>(P, A, site);
-                    }
-                    X.psi[site] = (float)psi_n;
-                }
-                ring[(slot * RH + w + 1) * RW + lane + 1] = psi_n;
-                if (fluid_n && inb && full) {
-                    mom_put(mn, mom + (k % 3) * 11 * mstride, mstride);
-                    coll_bits |= 1u << k;
-                }
-            }
-            __syncthreads();
-            if (pulling && tid == 0) {
-                __threadfence();
-                atomicExch(X.flags + (size_t)t * nplanes_max + k, epoch);
-            }
-            // collide plane z0 - 3 + k: psi of its planes z0 - 4 + k .. z0 - 2 + k is complete
-            if (k >= 3 && (coll_bits >> (k - 2) & 1u)) {
-                const int kc = k - 2;
-                const int zc = z0 - 1 + kc;
-                const int sc = sxy + nxy * zc;
-                auto nb = [&](int cx, int cy, int cz) -> T {
-                    return ring[(((kc + cz) & 7) * RH + (w + 1 + cy)) * RW + (lane + 1 + cx)];
-                };
-                T F[3] = {T(0), T(0), T(0)};
-#pragma unroll
-                for (int kk = 0; kk < L::NP; ++kk) {
-                    const int p = L::rep(kk);
-                    const int cx = L::cx(p), cy = L::cy(p), cz = L::cz(p);
-                    const T d = (T)L::w(p) * (nb(cx, cy, cz) - nb(-cx, -cy, -cz));
-                    if (cx) F[0] += cx > 0 ? d : -d;
-                    if (cy) F[1] += cy > 0 ? d : -d;
-                    if (cz) F[2] += cz > 0 ? d : -d;
-                }
-                F[0] *= T(3);
-                F[1] *= T(3);
-                F[2] *= T(3);
-                SiteMom<T> mb;
-                mom_get(mb, mom + (kc % 3) * 11 * mstride, mstride);
-                collide_moments<1, T>(ph, mb, F, [&](int i, T r, T g) {
-                    const int ir = i * np + sc;
-                    SP::store(B, ir, ir + Q * np, ph, L::cls(i), r, g);
-                });
-            }
-            if (pulling && w == WY - 1) {
-                // the last warp waits for the neighbours' plane k and fetches the ring edge
-                bool ok = true;
-                if (nbt >= 0) {
-                    const volatile int* f = X.flags + (size_t)nbt * nplanes_max + k;
-                    const int want = P.stall_test ? epoch + 1 : epoch;  // failure-path test: never published
-                    int it = 0;
-                    while (*f != want) {
-                        if (*(volatile int*)X.status != 0 || ++it > kXWaitLimit) {
-                            ok = false;
-                            break;
-                        }
-                        __nanosleep(32);
-                    }
-                    __threadfence();
-                }
-                if (!ok) atomicExch(X.status, 2);
-                __syncwarp();
-                const int ncell = 2 * RW + 2 * WY;
-                for (int c = lane; c < ncell; c += 32) {
-                    int gx, gy, rr, rc;
-                    if (c < 2 * RW) {
-                        const int top = c < RW;
-                        rc = top ? c : c - RW;
-                        rr = top ? 0 : WY + 1;
-                        gx = x0 - 1 + rc;
-                        gy = top ? y0 - 1 : y0 + WY;
-                    } else {
-                        const int c2 = c - 2 * RW;
-                        const int left = c2 < WY;
-                        rr = (left ? c2 : c2 - WY) + 1;
-                        rc = left ? 0 : RW - 1;
-                        gx = left ? x0 - 1 : x0 + 32;
-                        gy = y0 + rr - 1;
-                    }
-                    T v = psi_wall;
-                    if (zok && gx >= 0 && gx < nx && gy >= 0 && gy < ny) v = (T)__ldcg(X.psi + gx + nx * gy + nxy * zs);
-                    ring[(slot * RH + rr) * RW + rc] = v;
-                }
-            }
-        }
-        __syncthreads();  // the ring and moment slots are reused by the next tile
-    }
-    // the last block to finish rearms the tile counter and advances the epoch
-    if (tid == 0) {
-        __threadfence();
-        const int d = atomicAdd(X.ctl + 1, 1);
-        if (d == (int)gridDim.x - 1) {
-            atomicExch(X.ctl, 0);
-            atomicExch(X.ctl + 1, 0);
-            __threadfence();
-            atomicAdd(X.ctl + 2, 1);
-        }
-    }
-}
-
-// ------------------------------------------------- pipelined variants (variant 3)
-// The collision of row/plane k needs psi of k+1, so a plain march waits for the loads of
-// k+1 and only then computes.  The pipelined march collides k-2 while the loads of k are
-// in flight: iteration k issues the pull of k, collides k-2 (its psi neighbours k-3..k-1
-// are known), then finishes psi(k).  D2Q9 keeps three rows of populations in registers;
-// D3Q19 parks the waiting plane's populations in a per-thread shared-memory stage.
-
-template <int PREC, typename IDX>
-__global__ void __launch_bounds__(256) k_step_d2q9_pipe(const KParams P,
-                                                        const typename Store<PREC>::S* __restrict__ A,
-                                                        typename Store<PREC>::S* __restrict__ B,
-                                                        const uint32_t* __restrict__ link,
-                                                        const int* __restrict__ tiles)
-{
-    using T = typename Store<PREC>::T;
-    using L = Lat<0>;
-    constexpr int Q = 9;
-    const int lane = threadIdx.x & 31;
-    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    int sxi, syi;
-    if (!strip_of(P, tiles, gw, sxi, syi)) return;  // warp-uniform
-    const int nx = P.nx, ny = P.ny;
-    const int x = sxi * 30 + lane - 1;
-    int xs;
-    const bool xok = wrap_coord(x, nx, P.per[0], xs) && x <= nx;
-    const bool xint = lane >= 1 && lane <= 30 && x < nx;
-    Up u;
-    nbr_off(xs, nx, P.per[0], u.xm, u.xp);
-    u.zm = u.zp = 0;
-    const int y0 = syi * P.rows;
-    const int y1 = min(y0 + P.rows, ny);
-    const T psi_wall = phys<T>(P).psi_wall;
-
-    T psi_a = psi_wall, psi_b = psi_wall, psi_c = psi_wall;  // rows k-3, k-2, k-1
-    T r1[Q], g1[Q], r2[Q], g2[Q];                           // populations of rows k-1, k-2
-    bool c1 = false, c2 = false;
-    IDX s1 = 0, s2 = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) r1[i] = g1[i] = r2[i] = g2[i] = T(0);
-
-    for (int yy = y0 - 1; yy <= y1 + 1; ++yy) {
-        T rn[Q], gn[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) rn[i] = gn[i] = T(0);
-        T psi_n = psi_wall;
-        bool fluid_n = false;
-        IDX s = 0;
-        if (yy <= y1) {
-            int ys;
-            const bool yok = wrap_coord(yy, ny, P.per[1], ys);
-            int dym, dyp;
-            nbr_off(ys, ny, P.per[1], dym, dyp);
-            u.ym = (long long)dym * nx;
-            u.yp = (long long)dyp * nx;
-            s = (IDX)xs + (IDX)nx * (IDX)ys;
-            if (xok && yok) {
-                const uint32_t lk = link ? __ldg(link + s) : 0u;
-                const uint32_t type = (lk >> kTypeShift) & 3u;
-                if (type == kTypeFluid) {
-                    psi_n = pull_fluid<0, PREC, IDX>(P, A, s, u, lk, rn, gn);
-                    fluid_n = true;
-                } else if (type == kTypePort) {
-                    psi_n = ghost_psi<0, PREC, IDX>(P, A, s);
-                }
-            }
-        }
-        if (yy - 2 >= y0) {  // warp-uniform: collide row yy-2 with psi rows a, b, c
-            const T am = __shfl_up_sync(0xffffffffu, psi_a, 1), ap = __shfl_down_sync(0xffffffffu, psi_a, 1);
-            const T bm = __shfl_up_sync(0xffffffffu, psi_b, 1), bp = __shfl_down_sync(0xffffffffu, psi_b, 1);
-            const T cm = __shfl_up_sync(0xffffffffu, psi_c, 1), cp = __shfl_down_sync(0xffffffffu, psi_c, 1);
-            if (c2) {
-                auto nb = [&](int cx, int cy) -> T {
-                    return cy < 0 ? (cx < 0 ? am : (cx > 0 ? ap : psi_a))
-                         : cy > 0 ? (cx < 0 ? cm : (cx > 0 ? cp : psi_c))
-                                  : (cx < 0 ? bm : (cx > 0 ? bp : psi_b));
-                };
-                T F[3] = {T(0), T(0), T(0)};
-#pragma unroll
-                for (int k = 0; k < L::NP; ++k) {
-                    const int p = L::rep(k);
-                    const int cx = L::cx(p), cy = L::cy(p);
-                    const T d = (T)L::w(p) * (nb(cx, cy) - nb(-cx, -cy));
-                    if (cx) F[0] += cx > 0 ? d : -d;
-                    if (cy) F[1] += cy > 0 ? d : -d;
-                }
-                F[0] *= T(3);
-                F[1] *= T(3);
-                collide_site<0, T>(P, phys<T>(P), r2, g2, F);
-                store_site<0, PREC, IDX>(P, B, s2, r2, g2);
-            }
-        }
-        psi_a = psi_b;
-        psi_b = psi_c;
-        psi_c = psi_n;
-        c2 = c1;
-        s2 = s1;
-        c1 = fluid_n && xint && yy >= y0 && yy < y1;
-        s1 = s;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            r2[i] = r1[i];
-            g2[i] = g1[i];
-            r1[i] = rn[i];
-            g1[i] = gn[i];
-        }
-    }
-}
-
-// blockDim = (32, WY); smem: psi [4][WY][32], population stages [2][2Q][WY*32]
-template <int PREC, typename IDX>
-__global__ void __launch_bounds__(256, 2) k_step_d3q19_pipe(const KParams P,
-                                                            const typename Store<PREC>::S* __restrict__ A,
-                                                            typename Store<PREC>::S* __restrict__ B,
-                                                            const uint32_t* __restrict__ link,
-                                                            const int* __restrict__ tiles)
-{
-    int bx, by, z0, z1;
-    block_of(P, tiles, bx, by, z0, z1);
-    using T = typename Store<PREC>::T;
-    using L = Lat<1>;
-    constexpr int Q = 19;
-    extern __shared__ unsigned char smem_raw[];
-    const int lane = threadIdx.x;
-    const int w = threadIdx.y;
-    const int WY = blockDim.y;
-    const int nthr = 32 * WY;
-    const int tid = w * 32 + lane;
-    T* psi_s = reinterpret_cast<T*>(smem_raw);  // [4][WY][32]
-    T* stage = psi_s + 4 * nthr;                 // [2][2Q][nthr]
-    const int nx = P.nx, ny = P.ny, nz = P.nz;
-    const long long nxy = (long long)nx * ny;
-    const int x = bx * 30 + lane - 1;
-    const int y = by * (WY - 2) + w - 1;
-    int xs, ys;
-    const bool xok = wrap_coord(x, nx, P.per[0], xs) && x <= nx;
-    const bool yok = wrap_coord(y, ny, P.per[1], ys) && y <= ny;
-    const bool inner = lane >= 1 && lane <= 30 && x < nx && w >= 1 && w <= WY - 2 && y < ny;
-    Up u;
-    {
-        int a, b;
-        nbr_off(xs, nx, P.per[0], u.xm, u.xp);
-        nbr_off(ys, ny, P.per[1], a, b);
-        u.ym = (long long)a * nx;
-        u.yp = (long long)b * nx;
-    }
-    const IDX sxy = (IDX)xs + (IDX)nx * (IDX)ys;
-    const T psi_wall = phys<T>(P).psi_wall;
-    bool c1 = false, c2 = false;  // planes k-1, k-2 collide here
-
-    for (int zz = z0 - 1; zz <= z1 + 1; ++zz) {
-        T rn[Q], gn[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) rn[i] = gn[i] = T(0);
-        T psi_n = psi_wall;
-        bool fluid_n = false;
-        if (zz <= z1) {
-            int zs;
-            const bool zok = wrap_coord(zz, nz, P.per[2], zs);
-            int a, b;
-            nbr_off(zs, nz, P.per[2], a, b);
-            u.zm = (long long)a * nxy;
-            u.zp = (long long)b * nxy;
-            const IDX s = sxy + (IDX)nxy * (IDX)zs;
-            if (xok && yok && zok) {
-                const uint32_t lk = link ? __ldg(link + s) : 0u;
-                const uint32_t type = (lk >> kTypeShift) & 3u;
-                if (type == kTypeFluid) {
-                    psi_n = pull_fluid<1, PREC, IDX>(P, A, s, u, lk, rn, gn);
-                    fluid_n = true;
-                } else if (type == kTypePort) {
-                    psi_n = ghost_psi<1, PREC, IDX>(P, A, s);
-                }
-            }
-        }
-        if (c2) {  // collide plane zc = zz-2 (psi of zc-1..zc+1 are in shared memory)
-            const int zc = zz - 2;
-            T* st = stage + (size_t)(zc & 1) * 2 * Q * nthr;
-            T rc[Q], gc[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                rc[i] = st[i * nthr + tid];
-                gc[i] = st[(Q + i) * nthr + tid];
-            }
-            auto nb = [&](int cx, int cy, int cz) -> T {
-                const int slot = (zc + cz - z0 + 1) & 3;
-                return psi_s[(slot * WY + (w + cy)) * 32 + (lane + cx)];
-            };
-            T F[3] = {T(0), T(0), T(0)};
-#pragma unroll
-            for (int k = 0; k < L::NP; ++k) {
-                const int p = L::rep(k);
-                const int cx = L::cx(p), cy = L::cy(p), cz = L::cz(p);
-                const T d = (T)L::w(p) * (nb(cx, cy, cz) - nb(-cx, -cy, -cz));
-                if (cx) F[0] += cx > 0 ? d : -d;
-                if (cy) F[1] += cy > 0 ? d : -d;
-                if (cz) F[2] += cz > 0 ? d : -d;
-            }
-            F[0] *= T(3);
-            F[1] *= T(3);
-            F[2] *= T(3);
-            collide_site<1, T>(P, phys<T>(P), rc, gc, F);
-            store_site<1, PREC, IDX>(P, B, sxy + (IDX)nxy * (IDX)zc, rc, gc);
-        }
-        c2 = c1;
-        c1 = fluid_n && inner && zz >= z0 && zz < z1;
-        if (c1) {  // park plane zz's populations (same slot as the plane just collided)
-            T* st = stage + (size_t)(zz & 1) * 2 * Q * nthr;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                st[i * nthr + tid] = rn[i];
-                st[(Q + i) * nthr + tid] = gn[i];
-            }
-        }
-        if (zz <= z1) psi_s[(((zz - z0 + 1) & 3) * WY + w) * 32 + lane] = psi_n;
-        __syncthreads();
-    }
-}
-
-// ----------------------------------------------- asynchronous-copy variant (variant 4)
-// D3Q19, 4-byte storage formats.  Each thread copies the pulled populations of its site
-// for plane zz+2 into its own shared-memory stage with cp.async while it computes psi of
-// plane zz and collides plane zz-1, so loads are in flight during the arithmetic instead of
-// between it.  Stages: zz-1 (collided), zz (psi), zz+1, zz+2 (in flight) -> 4 per thread.
-// The link word of a plane is read one iteration before its copies are issued.
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-constexpr int kAsyncStages = 4;  // lookahead 2
-
-template <int PREC, typename IDX>
-__global__ void __launch_bounds__(256, 1) k_step_d3q19_async(const KParams P,
-                                                             const typename Store<PREC>::S* __restrict__ A,
-                                                             typename Store<PREC>::S* __restrict__ B,
-                                                             const uint32_t* __restrict__ link,
-                                                             const int* __restrict__ tiles)
-{
-    int bx, by, z0, z1;
-    block_of(P, tiles, bx, by, z0, z1);
-    using S = typename Store<PREC>::S;
-    using T = typename Store<PREC>::T;
-    using L = Lat<1>;
-    constexpr int Q = 19;
-    static_assert(sizeof(S) == 4, "4-byte storage only");
-    extern __shared__ unsigned char smem_raw[];
-    const int lane = threadIdx.x;
-    const int w = threadIdx.y;
-    const int WY = blockDim.y;
-    const int nthr = 32 * WY;
-    const int tid = w * 32 + lane;
-    T* psi_s = reinterpret_cast<T*>(smem_raw);        // [4][WY][32]
-    S* stage = reinterpret_cast<S*>(psi_s + 4 * nthr);  // [kAsyncStages][2Q][nthr]
-    const int nx = P.nx, ny = P.ny, nz = P.nz;
-    const long long nxy = (long long)nx * ny;
-    const int x = bx * 30 + lane - 1;
-    const int y = by * (WY - 2) + w - 1;
-    int xs, ys;
-    const bool xok = wrap_coord(x, nx, P.per[0], xs) && x <= nx;
-    const bool yok = wrap_coord(y, ny, P.per[1], ys) && y <= ny;
-    const bool inner = lane >= 1 && lane <= 30 && x < nx && w >= 1 && w <= WY - 2 && y < ny;
-    Up u;
-    {
-        int a, b;
-        nbr_off(xs, nx, P.per[0], u.xm, u.xp);
-        nbr_off(ys, ny, P.per[1], a, b);
-        u.ym = (long long)a * nx;
-        u.yp = (long long)b * nx;
-    }
-    const IDX sxy = (IDX)xs + (IDX)nx * (IDX)ys;
-    const IDX np = (IDX)P.np;
-    const Phys<T>& ph = phys<T>(P);
-    const T psi_wall = ph.psi_wall;
-    // site kind of a plane for this thread: 0 outside/wall, 1 fluid, 2 port ghost
-    auto kind_of = [&](int zz, uint32_t& lk, IDX& s, int& zs) -> int {
-        lk = 0;
-        s = 0;
-        zs = 0;
-        if (zz > z1) return 0;
-        const bool zok = wrap_coord(zz, nz, P.per[2], zs);
-        if (!(xok && yok && zok)) return 0;
-        s = sxy + (IDX)nxy * (IDX)zs;
-        lk = link ? __ldg(link + s) : 0u;
-        const uint32_t type = (lk >> kTypeShift) & 3u;
-        return type == kTypeFluid ? 1 : (type == kTypePort ? 2 : 0);
-    };
-    // issue the copies of plane zz (kind k) into its stage
-    auto issue = [&](int zz, int k, uint32_t lk, IDX s, int zs) {
-        S* st = stage + (size_t)((zz - z0 + 1) & (kAsyncStages - 1)) * 2 * Q * nthr;
-        if (k == 1) {
-            Up uu = u;
-            int a, b;
-            nbr_off(zs, nz, P.per[2], a, b);
-            uu.zm = (long long)a * nxy;
-            uu.zp = (long long)b * nxy;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const bool bounce = (lk >> i) & 1u;
-                const IDX ir = bounce ? (IDX)L::opp(i) * np + s : (IDX)i * np + s + up_off<1, IDX>(uu, i);
-                cp_async4(st + i * nthr + tid, A + ir);
-                cp_async4(st + (Q + i) * nthr + tid, A + ir + (IDX)Q * np);
-            }
-        } else if (k == 2) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const IDX ir = (IDX)i * np + s;
-                cp_async4(st + i * nthr + tid, A + ir);
-                cp_async4(st + (Q + i) * nthr + tid, A + ir + (IDX)Q * np);
-            }
-        }
-        cp_async_commit();
-    };
-    auto read_stage = [&](int zz, T (&r)[Q], T (&g)[Q]) {
-        const S* st = stage + (size_t)((zz - z0 + 1) & (kAsyncStages - 1)) * 2 * Q * nthr;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            // decode exactly as a global load would (Store::load on the staged element)
-            Store<PREC>::load(st, (IDX)(i * nthr + tid), (IDX)((Q + i) * nthr + tid), ph, L::cls(i), r[i], g[i]);
-        }
-    };
-
-    // prologue: planes z0-1 and z0 in flight, link of z0+1 known
-    int k_a, k_b, k_c, zs_a, zs_b, zs_c;
-    uint32_t lk_a, lk_b, lk_c;
-    IDX s_a, s_b, s_c;
-    k_a = kind_of(z0 - 1, lk_a, s_a, zs_a);
-    issue(z0 - 1, k_a, lk_a, s_a, zs_a);
-    k_b = kind_of(z0, lk_b, s_b, zs_b);
-    issue(z0, k_b, lk_b, s_b, zs_b);
-    k_c = kind_of(z0 + 1, lk_c, s_c, zs_c);
-    int kind_cur = k_a;       // kind of plane zz (for psi)
-    int kind_next = k_b;      // kind of plane zz+1
-    bool coll_b = false;      // plane zz-1 collides here
-    IDX sc_prev = 0;
-
-    for (int zz = z0 - 1; zz <= z1; ++zz) {
-        // 1. issue plane zz+2 (its link word was read last iteration), read the link of zz+3
-        issue(zz + 2, k_c, lk_c, s_c, zs_c);
-        const int kind_2 = k_c;
-        k_c = kind_of(zz + 3, lk_c, s_c, zs_c);
-        // 2. plane zz has landed (two newer groups may still be in flight)
-        cp_async_wait<2>();
-        T psi_n = psi_wall;
-        if (kind_cur != 0) {
-            T r[Q], g[Q];
-            read_stage(zz, r, g);
-            T rr = r[0], sg = g[0];
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                rr += r[i];
-                sg += g[i];
-            }
-            const T rho = ph.rho0 + sg;
-            psi_n = (rr - (rho - rr)) / rho;
-        }
-        psi_s[(((zz - z0 + 1) & 3) * WY + w) * 32 + lane] = psi_n;
-        __syncthreads();
-        // 3. collide plane zz-1
-        if (zz - 1 >= z0 && coll_b) {
-            const int zc = zz - 1;
-            T r[Q], g[Q];
-            read_stage(zc, r, g);
-            auto nb = [&](int cx, int cy, int cz) -> T {
-                const int slot = (zc + cz - z0 + 1) & 3;
-                return psi_s[(slot * WY + (w + cy)) * 32 + (lane + cx)];
-            };
-            T F[3] = {T(0), T(0), T(0)};
-#pragma unroll
-            for (int k = 0; k < L::NP; ++k) {
-                const int p = L::rep(k);
-                const int cx = L::cx(p), cy = L::cy(p), cz = L::cz(p);
-                const T d = (T)L::w(p) * (nb(cx, cy, cz) - nb(-cx, -cy, -cz));
-                if (cx) F[0] += cx > 0 ? d : -d;
-                if (cy) F[1] += cy > 0 ? d : -d;
-                if (cz) F[2] += cz > 0 ? d : -d;
-            }
-            F[0] *= T(3);
-            F[1] *= T(3);
-            F[2] *= T(3);
-            collide_site<1, T>(P, ph, r, g, F);
-            store_site<1, PREC, IDX>(P, B, sc_prev, r, g);
-        }
-        coll_b = kind_cur == 1 && inner && zz >= z0 && zz < z1;
-        sc_prev = sxy + (IDX)nxy * (IDX)(zz < 0 ? 0 : (zz >= nz ? 0 : zz));
-        kind_cur = kind_next;
-        kind_next = kind_2;
-    }
-    cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------- batched kernels
@@ -1718,33 +1172,48 @@ __global__ void __launch_bounds__(256, MINB) k_batch_d3q19(const BatchSlot* __re
     }
 }
 
-cudaError_t launch_batch_step(int lattice, int precision, const BatchSlot* slots, const BatchItem* items,
-                              const int* nitems, int k, cudaStream_t st)
+// the batched step kernel of (lattice, precision): f(kernel, threads per block, bytes of
+// dynamic shared memory per block) for block height wy (D3Q19)
+template <typename F>
+static cudaError_t with_batch_kernel(int lattice, int precision, int wy, F&& f)
 {
-    const int sms = 152;
     if (lattice == LBCG_D2Q9) {
-        const unsigned grid = sms * 3;
         switch (precision) {
-            case LBCG_FP64: k_batch_d2q9<LBCG_FP64><<<grid, 256, 0, st>>>(slots, items, nitems, k); break;
-            case LBCG_FP32: k_batch_d2q9<LBCG_FP32><<<grid, 256, 0, st>>>(slots, items, nitems, k); break;
-            case LBCG_FP32_DEV: k_batch_d2q9<LBCG_FP32_DEV><<<grid, 256, 0, st>>>(slots, items, nitems, k); break;
-            default: k_batch_d2q9<LBCG_FP16_SCALED><<<grid, 256, 0, st>>>(slots, items, nitems, k); break;
-        }
-    } else {
-        const dim3 block(32, 8);
-        const size_t sm4 = 4 * 8 * 32 * sizeof(float);
-        switch (precision) {
-            case LBCG_FP64:
-                k_batch_d3q19<LBCG_FP64, 2><<<sms * 2, block, 4 * 8 * 32 * sizeof(double), st>>>(slots, items, nitems, k);
-                break;
-            case LBCG_FP32: k_batch_d3q19<LBCG_FP32, 3><<<sms * 3, block, sm4, st>>>(slots, items, nitems, k); break;
-            case LBCG_FP32_DEV:
-                k_batch_d3q19<LBCG_FP32_DEV, 3><<<sms * 3, block, sm4, st>>>(slots, items, nitems, k);
-                break;
-            default: k_batch_d3q19<LBCG_FP16_SCALED, 3><<<sms * 3, block, sm4, st>>>(slots, items, nitems, k); break;
+            case LBCG_FP64: return f(k_batch_d2q9<LBCG_FP64>, 256, (size_t)0);
+            case LBCG_FP32: return f(k_batch_d2q9<LBCG_FP32>, 256, (size_t)0);
+            case LBCG_FP32_DEV: return f(k_batch_d2q9<LBCG_FP32_DEV>, 256, (size_t)0);
+            default: return f(k_batch_d2q9<LBCG_FP16_SCALED>, 256, (size_t)0);
         }
     }
-    return cudaGetLastError();
+    const int threads = 32 * wy;
+    const size_t sm4 = 4 * (size_t)threads * sizeof(float);
+    switch (precision) {
+        case LBCG_FP64: return f(k_batch_d3q19<LBCG_FP64, 2>, threads, 4 * (size_t)threads * sizeof(double));
+        case LBCG_FP32: return f(k_batch_d3q19<LBCG_FP32, 3>, threads, sm4);
+        case LBCG_FP32_DEV: return f(k_batch_d3q19<LBCG_FP32_DEV, 3>, threads, sm4);
+        default: return f(k_batch_d3q19<LBCG_FP16_SCALED, 3>, threads, sm4);
+    }
+}
+
+int batch_resident_blocks(int lattice, int precision, int wy)
+{
+    int dev = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    const cudaError_t e = with_batch_kernel(lattice, precision, wy, [&](auto kern, int threads, size_t smem) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem);
+    });
+    return e == cudaSuccess ? per : 0;
+}
+
+cudaError_t launch_batch_step(int lattice, int precision, const BatchSlot* slots, const BatchItem* items,
+                              const int* nitems, int k, int grid, int wy, cudaStream_t st)
+{
+    return with_batch_kernel(lattice, precision, wy, [&](auto kern, int threads, size_t smem) {
+        const dim3 block = lattice == LBCG_D2Q9 ? dim3(256) : dim3(32, wy);
+        (void)threads;
+        kern<<<(unsigned)grid, block, smem, st>>>(slots, items, nitems, k);
+        return cudaGetLastError();
+    });
 }
 
 // ---------------------------------------------------------------------- launchers
@@ -1765,13 +1234,6 @@ static cudaError_t launch_d2q9(lbcg_ctx* c, const void* a, void* b)
             k_step_d2q9_mom<PREC, int><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
         else
             k_step_d2q9_mom<PREC, long long><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
-        return cudaGetLastError();
-    }
-    if (c->variant == 3) {
-        if (small_index(c))
-            k_step_d2q9_pipe<PREC, int><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
-        else
-            k_step_d2q9_pipe<PREC, long long><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
         return cudaGetLastError();
     }
     if (small_index(c))
@@ -1860,62 +1322,6 @@ static cudaError_t launch_d3q19_tma(lbcg_ctx* c, const void* a, void* b)
     return cudaGetLastError();
 }
 
-// ----------------------------------------------------- psi-exchange march (host)
-static size_t xchg_smem(int wy) { return (8 * (size_t)(wy + 2) * 34 + 3 * 11 * 32 * (size_t)wy) * sizeof(float); }
-
-int xchg_resident_blocks(const lbcg_ctx* c)
-{
-    int dev = 0, sms = 0, per = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    const int threads = 32 * c->block_rows;
-    cudaError_t e;
-    switch (c->p.precision) {
-        case LBCG_FP32:
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_d3q19_xchg<LBCG_FP32>, threads,
-                                                              xchg_smem(c->block_rows));
-            break;
-        case LBCG_FP32_DEV:
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_d3q19_xchg<LBCG_FP32_DEV>, threads,
-                                                              xchg_smem(c->block_rows));
-            break;
-        case LBCG_FP16_SCALED:
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_d3q19_xchg<LBCG_FP16_SCALED>, threads,
-                                                              xchg_smem(c->block_rows));
-            break;
-        default: return 0;
-    }
-    return e == cudaSuccess ? per * sms : 0;
-}
-
-// Tables built and the progress bound met: more resident blocks than a tile's neighbours
-// span in list order (nsx + 2 columns) times the planes a tile can run ahead (rows + 2).
-bool xchg_supported(const lbcg_ctx* c)
-{
-    return c->d_xtiles && c->xntiles > 0 && c->xwy == c->block_rows && c->xrows == c->kp.rows &&
-           (long long)c->xgrid >= (long long)(c->xnsx + 2) * (c->xrows + 2) + 32 && small_index(c);
-}
-
-template <int PREC>
-static cudaError_t launch_d3q19_xchg(lbcg_ctx* c, const void* a, void* b)
-{
-    using S = typename Store<PREC>::S;
-    XParams X;
-    X.nsx = c->xnsx;
-    X.nsy = c->xnsy;
-    X.ntiles = c->xntiles;
-    X.rows = c->xrows;
-    X.tiles = c->d_xtiles;
-    X.map = c->d_xmap;
-    X.psi = c->d_psibuf;
-    X.flags = c->d_xflags;
-    X.ctl = c->d_xctl;
-    X.status = c->d_status;
-    k_step_d3q19_xchg<PREC><<<c->xgrid, dim3(32, c->block_rows), xchg_smem(c->block_rows), c->stream>>>(
-        c->kp, X, (const S*)a, (S*)b, c->d_link);
-    return cudaGetLastError();
-}
-
 template <int PREC, bool KEEP>
 static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant)
 {
@@ -1928,26 +1334,13 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant
     dim3 grid = tl ? dim3((unsigned)P.ntiles) : dim3(P.nsx, P.nsy, P.nsz);
     size_t smem = 4 * (size_t)wy * 32 * sizeof(T);
     const uint32_t* lk = c->any_link ? c->d_link : nullptr;
-    if constexpr (sizeof(S) == 4) {
-        if (variant == 4) {
-            const size_t smem4 = (4 * sizeof(T) + (size_t)kAsyncStages * 2 * 19 * sizeof(S)) * (size_t)wy * 32;
-            if (small_index(c)) {
-                cudaFuncSetAttribute(k_step_d3q19_async<PREC, int>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem4);
-                k_step_d3q19_async<PREC, int><<<grid, block, smem4, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
-            } else {
-                cudaFuncSetAttribute(k_step_d3q19_async<PREC, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem4);
-                k_step_d3q19_async<PREC, long long><<<grid, block, smem4, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
-            }
-            return cudaGetLastError();
-        }
-    }
+    const bool fuse = c->nghost > 0 && c->d_gstart && tl;
+    const PortTab pt{fuse ? c->d_ghost : nullptr, c->d_ghost_u, c->nghost, c->d_gstart, c->d_grow};
     if (variant == 7 && !KEEP) {
         const size_t smem7 = smem + 2 * 11 * (size_t)wy * 32 * sizeof(T);
         auto go = [&](auto kern) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem7);
-            kern<<<grid, block, smem7, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+            kern<<<grid, block, smem7, c->stream>>>(P, (const S*)a, (S*)b, lk, tl, pt);
         };
         if (small_index(c))
             go(k_step_d3q19_moms<PREC, int>);
@@ -1957,9 +1350,9 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant
     }
     if (variant == 6 && !KEEP) {
         if (small_index(c))
-            k_step_d3q19_mom<PREC, int><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+            k_step_d3q19_mom<PREC, int><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl, pt);
         else
-            k_step_d3q19_mom<PREC, long long><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+            k_step_d3q19_mom<PREC, long long><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl, pt);
         return cudaGetLastError();
     }
     if (variant == 5 && !KEEP) {
@@ -1967,18 +1360,6 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant
             k_step_d3q19_occ<PREC, int><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
         else
             k_step_d3q19_occ<PREC, long long><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
-        return cudaGetLastError();
-    }
-    if (variant == 3) {
-        const size_t smem3 = (4 + 2 * 2 * 19) * (size_t)wy * 32 * sizeof(T);
-        if (small_index(c)) {
-            cudaFuncSetAttribute(k_step_d3q19_pipe<PREC, int>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3);
-            k_step_d3q19_pipe<PREC, int><<<grid, block, smem3, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
-        } else {
-            cudaFuncSetAttribute(k_step_d3q19_pipe<PREC, long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem3);
-            k_step_d3q19_pipe<PREC, long long><<<grid, block, smem3, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
-        }
         return cudaGetLastError();
     }
     if (small_index(c))
@@ -1991,10 +1372,9 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant
 int effective_variant(const lbcg_ctx* c)
 {
     const int prec = c->p.precision;
-    // D2Q9: 3 the pipelined march; the moment march (6) by default for the regularized
-    // collision (measured fastest on large boxes); every other value the plain march
+    // D2Q9: the moment march (6) by default for the regularized collision (measured fastest
+    // on large boxes); every other value the plain march
     if (c->p.lattice == LBCG_D2Q9) {
-        if (c->variant == 3) return 3;
         return (c->variant == 0 || c->variant == 6) && c->p.collision == LBCG_REG ? 6 : 0;
     }
     // default (measured fastest): the moment march with its moments in registers; the BGK
@@ -2002,10 +1382,16 @@ int effective_variant(const lbcg_ctx* c)
     const bool reg = c->p.collision == LBCG_REG;
     int v = c->variant != 0 ? c->variant : (reg ? 6 : (prec == LBCG_FP64 ? 2 : 5));
     if (v == 8 && !tma_supported(c)) v = prec == LBCG_FP64 ? 6 : 7;
-    if (v == 10 && !xchg_supported(c)) v = 6;
     if ((v == 6 || v == 7) && !reg) v = prec == LBCG_FP64 ? 2 : 5;
-    if (v == 4 && prec != LBCG_FP32 && prec != LBCG_FP32_DEV) v = 2;
     return v;
+}
+
+// the step kernel refills the port ghosts of its output itself (the moment marches)
+bool step_fuses_ports(const lbcg_ctx* c)
+{
+    if (c->p.lattice != LBCG_D3Q19 || c->nghost == 0 || !c->d_gstart || !c->d_tiles) return false;
+    const int v = effective_variant(c);
+    return v == 6 || v == 7;
 }
 
 cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b)
@@ -2019,14 +1405,7 @@ cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b)
             case LBCG_FP16_SCALED: return launch_d2q9<LBCG_FP16_SCALED>(c, a, b);
         }
     } else {
-        // default: 5 (re-read, three blocks per SM; measured fastest) for 4- and 2-byte storage;
-        // FP64 re-reads with two blocks per SM (it spills at the three-block register budget)
         const int v = effective_variant(c);
-        if (v == 10) {
-            if (prec == LBCG_FP32) return launch_d3q19_xchg<LBCG_FP32>(c, a, b);
-            if (prec == LBCG_FP32_DEV) return launch_d3q19_xchg<LBCG_FP32_DEV>(c, a, b);
-            return launch_d3q19_xchg<LBCG_FP16_SCALED>(c, a, b);
-        }
         if (v == 8) {
             if (prec == LBCG_FP32) return launch_d3q19_tma<LBCG_FP32>(c, a, b);
             return launch_d3q19_tma<LBCG_FP32_DEV>(c, a, b);

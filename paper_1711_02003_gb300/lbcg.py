@@ -24,7 +24,9 @@ LBCG_OK = 0
 LBCG_D2Q9, LBCG_D3Q19 = 0, 1
 LBCG_FP64, LBCG_FP32, LBCG_FP32_DEV, LBCG_FP16_SCALED = 0, 1, 2, 3
 LBCG_REG, LBCG_BGK = 0, 1
+LBCG_ERR_STATE = -2  # call out of order (or a synchronous call on a capturing stream)
 LBCG_ERR_TIMEOUT = -9  # a bounded device-side wait or iteration ran out
+LBCG_ERR_BOUNDS = -10  # bounds-checked build: a step kernel met an index outside its array
 PRECISION_NAMES = {LBCG_FP64: "f64", LBCG_FP32: "f32", LBCG_FP32_DEV: "f32dev", LBCG_FP16_SCALED: "f16scaled"}
 ELEM_BYTES = {LBCG_FP64: 8, LBCG_FP32: 4, LBCG_FP32_DEV: 4, LBCG_FP16_SCALED: 2}
 
@@ -63,6 +65,7 @@ _PROTOS = {
     "lbcg_strerror": (C.c_char_p, [C.c_int]),
     "lbcg_last_error": (C.c_char_p, []),
     "lbcg_abi_version": (C.c_int, []),
+    "lbcg_bounds_checked": (C.c_int, []),
     "lbcg_state_bytes": (C.c_size_t, [C.POINTER(lbcg_params)]),
     "lbcg_create": (C.c_int, [C.POINTER(lbcg_params), _vp, C.POINTER(_vp)]),
     "lbcg_destroy": (None, [_vp]),
@@ -89,6 +92,8 @@ _PROTOS = {
     "lbcg_kernel_time": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong)]),
     "lbcg_set_launch": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
     "lbcg_get_launch": (C.c_int, [_vp, _ip, _ip, _ip]),
+    "lbcg_get_grid": (C.c_int, [_vp, C.POINTER(C.c_longlong), _ip, _ip]),
+    "lbcg_current_state": (_vp, [_vp]),
     "lbcg_fma_peak": (C.c_int, [C.c_int, _vp, _dp]),
     "lbcg_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp)]),
     "lbcg_batch_destroy": (None, [_vp]),
@@ -98,6 +103,8 @@ _PROTOS = {
     "lbcg_batch_step": (C.c_int, [_vp, C.c_longlong]),
     "lbcg_batch_poll": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(C.c_int)]),
     "lbcg_batch_last_error": (C.c_char_p, []),
+    "lbcg_batch_set_shape": (C.c_int, [_vp, _vp]),
+    "lbcg_batch_get_shape": (C.c_int, [_vp, _vp]),
 }
 
 
@@ -220,6 +227,18 @@ class Simulation:
         _check("lbcg_get_launch", _lib.lbcg_get_launch(self._h, C.byref(r), C.byref(b), C.byref(v)))
         return {"rows": r.value, "block_rows": b.value, "variant": v.value}
 
+    @property
+    def current_state_ptr(self) -> int:
+        """Device address of the buffer holding the current state (valid until the next step)."""
+        return int(_lib.lbcg_current_state(self._h) or 0)
+
+    @property
+    def grid(self) -> dict:
+        """Thread blocks and threads per block of the next step launch, kernels per step."""
+        b, t, k = C.c_longlong(), C.c_int(), C.c_int()
+        _check("lbcg_get_grid", _lib.lbcg_get_grid(self._h, C.byref(b), C.byref(t), C.byref(k)))
+        return {"blocks": b.value, "threads": t.value, "kernels_per_step": k.value}
+
     def init_fields(self, rho_r, rho_b, u=None):
         rr = np.ascontiguousarray(rho_r, np.float64).ravel()
         rb = np.ascontiguousarray(rho_b, np.float64).ravel()
@@ -339,11 +358,19 @@ def header_functions(header_path: str | None = None) -> list:
     return sorted(set(re.findall(r"\b(lbcg_[a-z0-9_]+)\s*\(", text)))
 
 
+class lbcg_batch_shape(C.Structure):
+    _fields_ = [("rows", C.c_int), ("block_rows", C.c_int), ("strips_per_item", C.c_int),
+                ("blocks_per_sm", C.c_int), ("graph_steps", C.c_int), ("sms", C.c_int)]
+
+
 class Batch:
     """Many instances of one lattice and storage precision advanced together
-    (lbcg_batch_*).  Instances are Simulation objects; they must use the batch's stream."""
+    (lbcg_batch_*).  Instances are Simulation objects; they must use the batch's stream.
+    ``shape``: a dict of lbcg_batch_shape fields (rows, block_rows, strips_per_item,
+    blocks_per_sm, graph_steps; missing or 0 = default)."""
 
-    def __init__(self, lattice: int, precision: int = LBCG_FP32_DEV, max_instances: int = 64, stream=None):
+    def __init__(self, lattice: int, precision: int = LBCG_FP32_DEV, max_instances: int = 64, stream=None,
+                 shape: dict | None = None):
         import torch
         L = load()
         self.lattice, self.precision = lattice, precision
@@ -355,6 +382,20 @@ class Batch:
         self._h = h
         self.max_instances = max_instances
         self.sims = {}
+        if shape:
+            self.set_shape(**shape)
+
+    def set_shape(self, rows: int = 0, block_rows: int = 0, strips_per_item: int = 0, blocks_per_sm: int = 0,
+                  graph_steps: int = 0, **_ignored):
+        sh = lbcg_batch_shape(int(rows), int(block_rows), int(strips_per_item), int(blocks_per_sm), int(graph_steps), 0)
+        self._bcheck("lbcg_batch_set_shape", _lib.lbcg_batch_set_shape(self._h, C.byref(sh)))
+
+    @property
+    def shape(self) -> dict:
+        """The launch shape after defaults (and the device's SM count)."""
+        sh = lbcg_batch_shape()
+        self._bcheck("lbcg_batch_get_shape", _lib.lbcg_batch_get_shape(self._h, C.byref(sh)))
+        return {f: getattr(sh, f) for f, _ in lbcg_batch_shape._fields_}
 
     @staticmethod
     def _bcheck(fn, st):

@@ -108,7 +108,9 @@ class Engine:
 class LbcgEngine(Engine):
     """The CUDA library: one lbcg batch per lattice on a shared stream."""
 
-    def __init__(self, precision: int = 2, max_slots: int = 64, stream=None):
+    def __init__(self, precision: int = 2, max_slots: int = 64, stream=None, shapes: dict | None = None):
+        """shapes: optional launch shape per lattice ({W.D2Q9: {...}, W.D3Q19: {...}}, fields of
+        lbcg_batch_shape), e.g. from autotune.autotune_batch."""
         import torch
 
         from . import lbcg
@@ -116,7 +118,9 @@ class LbcgEngine(Engine):
         lbcg.load()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.precision = precision
-        self.batches = {lat: lbcg.Batch(lat, precision, max_slots, stream=self.stream) for lat in (W.D2Q9, W.D3Q19)}
+        shapes = shapes or {}
+        self.batches = {lat: lbcg.Batch(lat, precision, max_slots, stream=self.stream, shape=shapes.get(lat))
+                        for lat in (W.D2Q9, W.D3Q19)}
         self.handles = {}
 
     def state_bytes(self, req: Request) -> int:

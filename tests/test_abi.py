@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_host_side_entry_points(lib):
-    assert lib.lbcg_abi_version() == 1
+    assert lib.lbcg_abi_version() == 2
     assert lib.lbcg_strerror(0) == b"ok"
     assert lib.lbcg_strerror(-5) == b"non-finite or non-positive density"
     pb = W.static_droplet(W.D2Q9, 64, 16)

@@ -1,11 +1,14 @@
 """lbcg_observables_noalloc: the allocation-free observables entry point.
 
-Some callers cannot allocate device memory (code recording a CUDA graph by stream
-capture, plug-ins whose host application owns every allocation, loops that forbid
-allocation after start-up).  This entry point needs no context and keeps its
-reduction scratch in a file-scope device array; these checks call it through the C
-ABI and compare it with lbcg_observables on the same state, twice in a row, so the
-shared scratch carries nothing from one call into the next."""
+Some callers cannot allocate device memory (plug-ins whose host application owns every
+allocation through its own pool, loops that forbid allocation after start-up, code running
+with the device memory budget fully committed).  This entry point needs no context and keeps
+its reduction scratch in a file-scope device array.  These checks call it through the C ABI
+on the buffer that holds a context's current state and compare it with lbcg_observables on
+the same state, in every storage precision and twice in a row (the shared scratch carries
+nothing from one call into the next), on a lattice large enough that the reduction grid is
+capped and its blocks stride over the sites, and on a stream that is being captured: the
+call is synchronous, so it must refuse there and leave the capture intact."""
 import ctypes as C
 
 import numpy as np
@@ -21,6 +24,8 @@ CASES = [
     ("step emulsifier D3Q19 70x20x12", lambda: W.step_emulsifier(nx=70, ny=20, nz=12, terrace_len=24,
                                                                    terrace_h=4, u_in=0.01, fill_x=12),
      (35, 10, 6), True),
+    # 327,680 sites: more than 1024 blocks of 256 sites, so the grid is capped and strides
+    ("droplet D2Q9 640x512", lambda: W.static_droplet(W.D2Q9, 640, 100, ny=512), (320, 256, 0), False),
 ]
 
 
@@ -35,26 +40,31 @@ def lb():
     return lbcg
 
 
-def _noalloc(lb, sim, mask_dev, centre, r_in=-1.0, r_out=-1.0):
+def _call(lb, sim, mask_dev, centre, r_in=-1.0, r_out=-1.0, stream=None):
     L = lb.load()
     out = lb.lbcg_obs()
     c = (C.c_double * 3)(*[float(v) for v in centre])
-    st = L.lbcg_observables_noalloc(C.byref(sim._p), C.c_void_p(sim._a.data_ptr()),
-                                    None if mask_dev is None else C.c_void_p(mask_dev.data_ptr()), c,
-                                    float(r_in), float(r_out), C.c_void_p(sim.stream.cuda_stream), C.byref(out))
-    assert st == 0, L.lbcg_last_error().decode()
+    st = (stream or sim.stream).cuda_stream
+    status = L.lbcg_observables_noalloc(C.byref(sim._p), C.c_void_p(sim.current_state_ptr),
+                                        None if mask_dev is None else C.c_void_p(mask_dev.data_ptr()), c,
+                                        float(r_in), float(r_out), C.c_void_p(st), C.byref(out))
+    return status, out
+
+
+def _noalloc(lb, sim, mask_dev, centre, r_in=-1.0, r_out=-1.0):
+    status, out = _call(lb, sim, mask_dev, centre, r_in, r_out)
+    assert status == 0, lb.load().lbcg_last_error().decode()
     return out
 
 
 @pytest.mark.parametrize("name,make,centre,use_mask", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_noalloc_matches_lbcg_observables(lb, name, make, centre, use_mask, precision):
     pb = make()
     sim = lb.Simulation(pb, precision)
     mask_dev = torch.from_numpy(np.ascontiguousarray(pb.mask, np.uint8)).cuda() if use_mask else None
-    for call in range(2):
-        # an even number of steps since binding leaves the current state in the first buffer
-        sim.step(64)
+    for call, steps in enumerate((33, 64)):   # odd, then even: the current state is in either buffer
+        sim.step(steps)
         for r_in, r_out in ((-1.0, -1.0), (3.0, 8.0)):
             ref = sim.observables(centre, r_in, r_out)
             out = _noalloc(lb, sim, mask_dev, centre, r_in, r_out)
@@ -66,6 +76,26 @@ def test_noalloc_matches_lbcg_observables(lb, name, make, centre, use_mask, prec
             assert out.nonfinite == 0 and out.step == -1
 
 
+def test_noalloc_refuses_a_capturing_stream(lb):
+    pb = W.static_droplet(W.D2Q9, 32, 8)
+    sim = lb.Simulation(pb, lb.LBCG_FP32_DEV)
+    sim.step(3)
+    before = _noalloc(lb, sim, None, (16, 16, 0))
+    x = torch.zeros(4, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.graph(graph, stream=side):
+        x.add_(1.0)
+        status, _ = _call(lb, sim, None, (16, 16, 0), stream=side)
+    assert status == lb.LBCG_ERR_STATE, status
+    assert "captured" in lb.load().lbcg_last_error().decode()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert x.tolist() == [1.0] * 4          # the capture ended cleanly and replays
+    after = _noalloc(lb, sim, None, (16, 16, 0))
+    assert after.mass_r == before.mass_r and after.dp == before.dp
+
+
 def test_noalloc_rejects_invalid_parameters(lb):
     pb = W.static_droplet(W.D2Q9, 16, 4)
     sim = lb.Simulation(pb, 2)
@@ -74,6 +104,6 @@ def test_noalloc_rejects_invalid_parameters(lb):
     L = lb.load()
     out = lb.lbcg_obs()
     c = (C.c_double * 3)(8.0, 8.0, 0.0)
-    assert L.lbcg_observables_noalloc(C.byref(p), C.c_void_p(sim._a.data_ptr()), None, c, -1.0, -1.0, None,
+    assert L.lbcg_observables_noalloc(C.byref(p), C.c_void_p(sim.current_state_ptr), None, c, -1.0, -1.0, None,
                                       C.byref(out)) == -1
     assert L.lbcg_observables_noalloc(C.byref(sim._p), None, None, c, -1.0, -1.0, None, C.byref(out)) == -1
