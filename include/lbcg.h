@@ -336,18 +336,21 @@ int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
  * 8 (D3Q19, regularized, FP32 or FP32-dev storage, nx a multiple of 4, block_rows 6 or
  * 8) the moment march with every plane's pulled populations staged in shared memory by
  * the tensor memory accelerator (two-stage pipeline of Q boxes per plane, bounded
- * waits); where its conditions do not hold it runs as 7 (FP64: 6).  The D3Q19 moment
- * marches (6, 7) refill the port ghosts of the state they write themselves (each block
- * after its tile, from the populations it has just written), so a step with ports is one
- * launch; the other variants run the separate refill kernel before each step.
- * Variants 6 and 7 fall back to 5 (FP64: 2) for the BGK collision.  A context created while
+ * waits); where its conditions do not hold it runs as 7 (FP64: 6), 9 (D3Q19, regularized,
+ * block_rows 3..8) variant 6 with each warp waiting per plane only for the two warps whose
+ * psi rows it reads (named barriers) instead of the whole block: identical results, warps
+ * up to one plane apart.  The D3Q19 moment marches (6, 7, 9) refill the port ghosts of the
+ * state they write themselves (each block after its tile, from the populations it has just
+ * written), so a step with ports is one launch; the other variants run the separate refill
+ * kernel before each step.
+ * Variants 6, 7 and 9 fall back to 5 (FP64: 2) for the BGK collision.  A context created while
  * the environment variable LBCG_TEST_PIPELINE_STALL=1 is set makes every pipeline wait of
  * variant 8 run out (failure-path test): the step then leaves the state invalid and
  * lbcg_synchronize and the read-back calls report LBCG_ERR_TIMEOUT once.  The default is the
  * moment march (6) for the regularized collision on either lattice; with BGK the plain
  * march for D2Q9 and variant 5 (FP64: 2) for D3Q19.  D2Q9 takes 6 (moment march,
  * regularized only) and treats every other value as the plain march.  Values 3, 4 and
- * above 8 are rejected (LBCG_ERR_ARG).
+ * above 9 are rejected (LBCG_ERR_ARG).
  * Within one variant results are bit-identical across shapes; variants may contract
  * multiply-adds and order sums differently and agree to
  * rounding.  Drops captured step graphs. */

@@ -11,9 +11,10 @@ Candidates:
          1 plain march} (short strips give small boxes enough warps)
   D3Q19: warps per block along y in {4, 6, 8} x z-planes per block in {4, 8, 16} x
          variant; regularized collision {7, 6 moment march (shared-memory / register
-         moments), 5 re-read}, plus 12 and 16 warps per block for variant 7 and the
-         TMA-staged march (variant 8; 6 or 8 warps, 8 or 16 planes) for 4-byte storage; BGK
-         {5, 1, 2}; FP64 regularized {6, 7, 2}, BGK {2, 1}
+         moments), 5 re-read}, plus 12 and 16 warps per block for variant 7, the moment march
+         with neighbour-only plane barriers (variant 9; 6 or 8 warps) and the TMA-staged march
+         (variant 8; 6 or 8 warps, 8 or 16 planes) for 4-byte storage; BGK {5, 1, 2}; FP64
+         regularized {6, 7, 2, 9 (6 or 8 warps)}, BGK {2, 1}
 
 autotune_batch times the batched kernels' launch shapes (work-item cut, resident blocks per
 SM, steps per captured graph) on a set of instances, such as a sample of the serving mix.
@@ -44,6 +45,8 @@ def candidates(lattice: int, precision: int, collision: int = 0) -> list:
     else:
         variants = [2, 1] if f64 else [5, 1, 2]
     out = [dict(rows=r, block_rows=b, variant=v) for v, b, r in itertools.product(variants, (4, 6, 8), (4, 8, 16))]
+    if collision == 0:
+        out += [dict(rows=r, block_rows=b, variant=9) for b, r in itertools.product((6, 8), (4, 8, 16))]
     if 7 in variants:
         out += [dict(rows=r, block_rows=b, variant=7) for b, r in itertools.product((12, 16), (4, 8))]
         if lbcg.ELEM_BYTES[precision] == 4:  # TMA-staged march (runs as 7 where it does not apply)

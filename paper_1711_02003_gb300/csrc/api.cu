@@ -1145,9 +1145,9 @@ int lbcg_set_launch(lbcg_ctx* c, int rows, int block_rows, int variant)
     // blocks of up to 512 threads; every other kernel up to 256
     const int max_wy = variant == 7 && c->p.collision == LBCG_REG ? 16 : 8;
     if (rows < 0 || block_rows < 0 || (block_rows > 0 && (block_rows < 3 || block_rows > max_wy)) || variant < 0 ||
-        variant > 8 || variant == 3 || variant == 4)
+        variant > 9 || variant == 3 || variant == 4)
         return fail(LBCG_ERR_ARG,
-                    "launch shape out of range (block_rows in 3..8, 3..16 with variant 7; variant in 0..2, 5..8)");
+                    "launch shape out of range (block_rows in 3..8, 3..16 with variant 7; variant in 0..2, 5..9)");
     c->rows = rows;
     c->block_rows = block_rows;
     c->variant = variant;

@@ -467,6 +467,31 @@ __device__ __forceinline__ void refill_tile_ports(const KParams& P, typename Sto
         fill_one<1, PREC>(P, B, pt.tab, pt.gu, pt.ng, pt.grow[e]);
 }
 
+// ---------------------------------------------------------- neighbour-only plane barrier
+// Warp w of a march reads the psi rows of warps w - 1 and w + 1 only, so instead of a block
+// barrier per plane the warps exchange signals with their two neighbours through named
+// barriers of 64 threads: B_w (id 1 + w) carries w's "psi written" to w + 1, A_w (id WY + w)
+// carries w + 1's to w.  Each warp signals up, waits on the warp below, signals down, waits
+// on the warp above: no warp's signal depends on another warp's wait (no chain), and a warp
+// signals a barrier again only after its partner has consumed the previous generation.  A
+// warp runs at most one plane ahead of its neighbours, which the four-slot psi ring allows.
+// Needs 2 (WY - 1) <= 15 barriers: WY <= 8.
+__device__ __forceinline__ void bar_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_sync_n(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void neighbour_sync(int w, int WY)
+{
+    if (w < WY - 1) bar_arrive(1 + w, 64);        // psi of w written: tell w + 1
+    if (w > 0) bar_sync_n(w, 64);                 // w - 1 has written
+    if (w > 0) bar_arrive(WY + w - 1, 64);        // tell w - 1
+    if (w < WY - 1) bar_sync_n(WY + w, 64);       // w + 1 has written
+}
+
 // ------------------------------------------------- moment march (variants 6, 7; regularized)
 template <typename T>
 __device__ __forceinline__ void mom_put(const SiteMom<T>& m, T* p, int st)
@@ -551,7 +576,7 @@ __device__ __forceinline__ typename Store<PREC>::T pull_moments(const KParams& P
 // only (the BGK update needs the individual populations).  MSMEM parks the waiting
 // moments in a thread-private shared-memory slot (two slots, alternating by plane)
 // instead of registers, for a smaller register budget.
-template <int PREC, typename IDX, bool MSMEM>
+template <int PREC, typename IDX, bool MSMEM, bool PAIR = false>
 __device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename Store<PREC>::S* __restrict__ A,
                                                typename Store<PREC>::S* __restrict__ B,
                                                const uint32_t* __restrict__ link, int bx, int by, int z0, int z1,
@@ -622,7 +647,10 @@ __device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename 
         const int slot_n = (zz - z0 + 1) & 3;
         ring_put(P, psi_s, (slot_n * WY + w) * 32 + lane, psi_n);
         if (MSMEM && fluid_n && full) mom_put(mn, mom_s + (zz & 1) * 11 * mstride, mstride);
-        __syncthreads();
+        if (PAIR && WY <= 8)
+            neighbour_sync(w, WY);
+        else
+            __syncthreads();
         if (zz - 1 >= z0 && coll_b) {
             const int zc = zz - 1;
             const IDX sc = sxy + (IDX)nxy * (IDX)zc;
@@ -667,6 +695,22 @@ __global__ void __launch_bounds__(256, PREC == LBCG_FP64 ? 2 : 3) k_step_d3q19_m
     int bx, by, z0, z1;
     block_of(P, tiles, bx, by, z0, z1);
     tile_d3q19_mom<PREC, IDX, false>(P, A, B, link, bx, by, z0, z1, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+    if (pt.tab) refill_tile_ports<PREC>(P, B, pt, (int)blockIdx.x);
+}
+
+// variant 9: variant 6 with neighbour-only plane barriers
+template <int PREC, typename IDX>
+__global__ void __launch_bounds__(256, PREC == LBCG_FP64 ? 2 : 3) k_step_d3q19_momn(const KParams P,
+                                                           const typename Store<PREC>::S* __restrict__ A,
+                                                           typename Store<PREC>::S* __restrict__ B,
+                                                           const uint32_t* __restrict__ link, const int* __restrict__ tiles,
+                                                           const PortTab pt)
+{
+    extern __shared__ unsigned char smem_raw[];
+    int bx, by, z0, z1;
+    block_of(P, tiles, bx, by, z0, z1);
+    tile_d3q19_mom<PREC, IDX, false, true>(P, A, B, link, bx, by, z0, z1,
+                                           reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
     if (pt.tab) refill_tile_ports<PREC>(P, B, pt, (int)blockIdx.x);
 }
 
@@ -1348,6 +1392,13 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant
             go(k_step_d3q19_moms<PREC, long long>);
         return cudaGetLastError();
     }
+    if (variant == 9 && !KEEP) {
+        if (small_index(c))
+            k_step_d3q19_momn<PREC, int><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl, pt);
+        else
+            k_step_d3q19_momn<PREC, long long><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl, pt);
+        return cudaGetLastError();
+    }
     if (variant == 6 && !KEEP) {
         if (small_index(c))
             k_step_d3q19_mom<PREC, int><<<grid, block, smem, c->stream>>>(P, (const S*)a, (S*)b, lk, tl, pt);
@@ -1382,7 +1433,7 @@ int effective_variant(const lbcg_ctx* c)
     const bool reg = c->p.collision == LBCG_REG;
     int v = c->variant != 0 ? c->variant : (reg ? 6 : (prec == LBCG_FP64 ? 2 : 5));
     if (v == 8 && !tma_supported(c)) v = prec == LBCG_FP64 ? 6 : 7;
-    if ((v == 6 || v == 7) && !reg) v = prec == LBCG_FP64 ? 2 : 5;
+    if ((v == 6 || v == 7 || v == 9) && !reg) v = prec == LBCG_FP64 ? 2 : 5;
     return v;
 }
 
@@ -1391,7 +1442,7 @@ bool step_fuses_ports(const lbcg_ctx* c)
 {
     if (c->p.lattice != LBCG_D3Q19 || c->nghost == 0 || !c->d_gstart || !c->d_tiles) return false;
     const int v = effective_variant(c);
-    return v == 6 || v == 7;
+    return v == 6 || v == 7 || v == 9;
 }
 
 cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b)

@@ -32,7 +32,7 @@ cases = [
      [{}, dict(variant=5), dict(variant=7, block_rows=12, rows=5), dict(variant=1, block_rows=4, rows=3)]),
     (W.step_emulsifier(nx=64, ny=30, nz=10, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10), 60,
      [{}, dict(variant=5), dict(variant=7, block_rows=6, rows=3), dict(variant=8, block_rows=8, rows=4),
-      dict(variant=2, block_rows=5, rows=7)]),
+      dict(variant=2, block_rows=5, rows=7), dict(variant=9, block_rows=4, rows=5)]),
     (W.static_droplet(W.D2Q9, 61, 9, ny=37, tau_r=1.7, tau_b=0.8), 50, [{}, dict(variant=1, rows=3)]),
     (W.cross_junction(nx=130, channel_w=16, side_x=40, side_len=12, fill_x=30), 60, [{}, dict(variant=1, rows=5)]),
 ]

@@ -192,6 +192,25 @@ def test_fused_port_refill_equals_refill_launch():
             assert pops_diff(a.populations(), b.populations(), prob) <= tol, (prob.name, prec)
 
 
+# The moment march with neighbour-only plane barriers (variant 9) lets the warps of a block run
+# up to one plane apart; it computes what the block-barrier march (variant 6) computes, so the
+# two agree bit for bit on walled, ported and periodic boxes at every block height.
+@pytest.mark.parametrize("block_rows,rows", [(8, 8), (5, 3), (3, 7)])
+def test_neighbour_barrier_march_equals_moment_march(block_rows, rows):
+    lb = _lb()
+    probs = [W.step_emulsifier(nx=64, ny=30, nz=10, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10),
+             W.static_droplet(W.D3Q19, 32, 8, centre=(15.5, 15.5, 15.5)),
+             W.static_droplet(W.D3Q19, 40, 9, ny=20, nz=18, centre=(19.5, 9.5, 8.5))]
+    for prob in probs:
+        for prec in (lb.LBCG_FP64, lb.LBCG_FP32_DEV, lb.LBCG_FP16_SCALED):
+            a = lb.Simulation(prob, prec, rows=rows, block_rows=block_rows, variant=6)
+            b = lb.Simulation(prob, prec, rows=rows, block_rows=block_rows, variant=9)
+            assert b.launch["variant"] == 9, b.launch
+            a.step(40)
+            b.step(40)
+            assert np.array_equal(state(a.populations(), prob), state(b.populations(), prob)), (prob.name, prec)
+
+
 # The TMA-staged moment march (variant 8) pulls through shared-memory boxes but computes
 # exactly what the register-pulling moment march (variant 7) computes: identical bits on
 # walled, ported and periodic boxes (periodic edges take the global-load path).
@@ -325,7 +344,8 @@ def _ported_emulsifier():
 
 
 @pytest.mark.parametrize("shape", [{}, dict(rows=8, block_rows=8, variant=6), dict(rows=4, block_rows=6, variant=7),
-                                   dict(rows=8, block_rows=8, variant=5)], ids=["default", "v6", "v7", "v5"])
+                                   dict(rows=8, block_rows=8, variant=5), dict(rows=8, block_rows=8, variant=9)],
+                         ids=["default", "v6", "v7", "v5", "v9"])
 def test_ported_step_emulsifier_1000_steps(shape):
     lb = _lb()
     pb, f, (orr, ob, ou) = _ported_emulsifier()
