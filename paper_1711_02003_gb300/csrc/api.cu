@@ -313,10 +313,34 @@ static void free_tables(lbcg_ctx* c)
     cudaFree(c->d_link);
     cudaFree(c->d_ghost);
     cudaFree(c->d_ghost_u);
+    cudaFree(c->d_gpsi);
     c->d_link = nullptr;
     c->d_ghost = nullptr;
     c->d_ghost_u = nullptr;
+    c->d_gpsi = nullptr;
+    c->gpsi_buf[0] = c->gpsi_buf[1] = nullptr;
 }
+
+namespace lbcg {
+
+// The table of a buffer stays with it while it is one of the two state buffers; a buffer
+// met for the first time (first use, or new buffers bound) takes a table whose buffer is no
+// longer a state buffer.  Every step reads the table of its input only after a refill of
+// that buffer's ghosts wrote it (the refill launch, or the previous step's fused refill).
+void* gpsi_for(lbcg_ctx* c, const void* buf)
+{
+    if (!c->d_gpsi || !buf) return nullptr;
+    for (int k = 0; k < 2; ++k)
+        if (c->gpsi_buf[k] == buf) return c->d_gpsi + (size_t)k * c->nghost;
+    for (int k = 0; k < 2; ++k)
+        if (c->gpsi_buf[k] != c->A && c->gpsi_buf[k] != c->B) {
+            c->gpsi_buf[k] = buf;
+            return c->d_gpsi + (size_t)k * c->nghost;
+        }
+    return nullptr;
+}
+
+}  // namespace lbcg
 
 extern "C" {
 
@@ -513,6 +537,10 @@ int lbcg_set_geometry(lbcg_ctx* c, const uint8_t* mask, const lbcg_port* ports, 
     }
     // ghost table: [site | inward neighbour | port | kind] and [ux | uy | uz | rho | psi]
     const int ng = (int)ghosts.size();
+    // D3Q19: the port site's link word carries its ghost-table row (the ghost-psi table)
+    const bool gpsi = c->p.lattice == LBCG_D3Q19 && ng > 0 && (long long)ng <= (long long)kGhostMask + 1;
+    if (gpsi)
+        for (int t = 0; t < ng; ++t) link[(size_t)ghosts[t]] |= (uint32_t)t;
     std::vector<int> tab((size_t)4 * std::max(ng, 1));
     std::vector<double> gu((size_t)5 * std::max(ng, 1));
     for (int t = 0; t < ng; ++t) {
@@ -550,7 +578,8 @@ int lbcg_set_geometry(lbcg_ctx* c, const uint8_t* mask, const lbcg_port* ports, 
         return fail(LBCG_ERR_NOMEM, "link table allocation failed");
     if (ng > 0) {
         if (cudaMalloc(&c->d_ghost, sizeof(int) * tab.size()) != cudaSuccess ||
-            cudaMalloc(&c->d_ghost_u, sizeof(double) * gu.size()) != cudaSuccess) {
+            cudaMalloc(&c->d_ghost_u, sizeof(double) * gu.size()) != cudaSuccess ||
+            (gpsi && cudaMalloc(&c->d_gpsi, sizeof(double) * 2 * (size_t)ng) != cudaSuccess)) {
             free_tables(c);
             return fail(LBCG_ERR_NOMEM, "port table allocation failed");
         }

@@ -65,11 +65,12 @@ constexpr int kFillThreads = 64;
 template <int LAT, int PREC>
 __global__ void __launch_bounds__(kFillThreads) k_fill_ports(const KParams P, typename Store<PREC>::S* __restrict__ a,
                                                              const int* __restrict__ tab,
-                                                             const double* __restrict__ gu, int ng)
+                                                             const double* __restrict__ gu, int ng,
+                                                             typename Store<PREC>::T* __restrict__ gpsi)
 {
     const int t = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (t >= ng) return;
-    fill_one<LAT, PREC>(P, a, tab, gu, ng, t);
+    fill_one<LAT, PREC>(P, a, tab, gu, ng, t, gpsi);
 }
 
 // batched refill: work item (slot, first ghost, count <= kFillThreads), one thread per
@@ -285,9 +286,12 @@ cudaError_t launch_fill_ports(lbcg_ctx* c, void* a)
 {
     if (c->nghost == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((c->nghost + kFillThreads - 1) / kFillThreads);  // a thread per ghost
+    // the ghost-psi table of buffer a (D3Q19 with a table), read by the marches' port lanes
+    void* gpsi = c->p.lattice == LBCG_D3Q19 ? gpsi_for(c, a) : nullptr;
 #define F_(LAT, PREC)                                                                                   \
     k_fill_ports<LAT, PREC><<<blocks, kFillThreads, 0, c->stream>>>(c->kp, (SOf<PREC>*)a, c->d_ghost, \
-                                                                    c->d_ghost_u, c->nghost)
+                                                                    c->d_ghost_u, c->nghost,          \
+                                                                    (typename Store<PREC>::T*)gpsi)
     LBCG_DISPATCH(c, F_);
 #undef F_
     return cudaGetLastError();

@@ -131,12 +131,17 @@ struct StorePlain {
         r = fr;
         g = (fr + fb) - ph.wr0[c];
     }
+    // the two stored values of one direction (what store writes)
+    __device__ static __forceinline__ void encode(T r, T g, const Phys<T>& ph, int c, S& fr, S& fb)
+    {
+        fr = (S)r;
+        fb = (S)((g + ph.wr0[c]) - r);
+    }
     template <typename IDX>
     __device__ static __forceinline__ void store(S* __restrict__ b, IDX ir, IDX ig, const Phys<T>& ph, int c, T r,
                                                  T g)
     {
-        b[ir] = (S)r;
-        b[ig] = (S)((g + ph.wr0[c]) - r);
+        encode(r, g, ph, c, b[ir], b[ig]);
     }
     // register form of the two stored values of one direction (as load)
     __device__ static __forceinline__ void decode(S fr_, S fb_, const Phys<T>& ph, int c, T& r, T& g)
@@ -162,6 +167,11 @@ struct Store<LBCG_FP32_DEV> {
     {
         r = a[ir];
         g = a[ig];
+    }
+    __device__ static __forceinline__ void encode(T r, T g, const Phys<T>&, int, S& fr, S& fg)
+    {
+        fr = r;
+        fg = g;
     }
     template <typename IDX>
     __device__ static __forceinline__ void store(S* __restrict__ b, IDX ir, IDX ig, const Phys<T>&, int, T r, T g)
@@ -197,13 +207,17 @@ struct Store<LBCG_FP16_SCALED> {
         r = __half2float(fr) * wi + 0.5f * ph.wr0[c];
         g = __half2float(fg) * (wi * ph.inv_scale_g);
     }
+    __device__ static __forceinline__ void encode(T r, T g, const Phys<T>& ph, int c, S& fr, S& fg)
+    {
+        const float iw = ph.inv_w[c];
+        fr = __float2half_rn((r - 0.5f * ph.wr0[c]) * iw);
+        fg = __float2half_rn(g * (iw * ph.scale_g));
+    }
     template <typename IDX>
     __device__ static __forceinline__ void store(S* __restrict__ b, IDX ir, IDX ig, const Phys<T>& ph, int c, T r,
                                                  T g)
     {
-        const float iw = ph.inv_w[c];
-        b[ir] = __float2half_rn((r - 0.5f * ph.wr0[c]) * iw);
-        b[ig] = __float2half_rn(g * (iw * ph.scale_g));
+        encode(r, g, ph, c, b[ir], b[ig]);
     }
 };
 
@@ -525,6 +539,40 @@ __device__ __forceinline__ void collide_moments(const Phys<T>& ph, const SiteMom
     out(0, rhoR - rsum, g0);
 }
 
+// psi of a port ghost site from its own populations: the rest population, then opposite
+// pairs (one summation order for every kernel and for the refill's ghost-psi table)
+template <int LAT, typename T, typename LD>
+__device__ __forceinline__ T ghost_psi_from(const Phys<T>& ph, LD&& ld)
+{
+    using L = Lat<LAT>;
+    T rr, sg;
+    ld(0, rr, sg);
+#pragma unroll
+    for (int k = 0; k < L::NP; ++k) {
+        const int p = L::rep(k);
+        T rp, gp, rq, gq;
+        ld(p, rp, gp);
+        ld(L::opp(p), rq, gq);
+        rr += rp + rq;
+        sg += gp + gq;
+    }
+    const T rho = ph.rho0 + sg;
+    return (rr - (rho - rr)) / rho;
+}
+
+template <int LAT, int PREC, typename IDX>
+__device__ __forceinline__ typename Store<PREC>::T ghost_psi(const KParams& P,
+                                                             const typename Store<PREC>::S* __restrict__ A, IDX s)
+{
+    using L = Lat<LAT>;
+    using T = typename Store<PREC>::T;
+    const IDX np = (IDX)P.np;
+    return ghost_psi_from<LAT, T>(phys<T>(P), [&](int i, T& r, T& g) {
+        const IDX ir = (IDX)i * np + s;
+        load_pop<PREC, IDX>(P, A, ir, ir + (IDX)L::Q * np, phys<T>(P), L::cls(i), r, g);
+    });
+}
+
 // ------------------------------------------------------------ port ghost refill
 // Ghost g of port m, inward neighbour x' (a fluid site):
 //   velocity:      f^k = f^{k,eq}(chi^k rho', u_port) + chi^k (f(x') - f^eq(x'))
@@ -539,7 +587,8 @@ __device__ __forceinline__ void collide_moments(const Phys<T>& ph, const SiteMom
 // and the pressure rule reduces to f^k_i(x') + (rho_port / rho' - 1) f^{k,eq}_i(x').
 template <int LAT, int PREC>
 __device__ __forceinline__ void fill_one(const KParams& P, typename Store<PREC>::S* __restrict__ a,
-                                         const int* __restrict__ tab, const double* __restrict__ gu, int ng, int t)
+                                         const int* __restrict__ tab, const double* __restrict__ gu, int ng, int t,
+                                         typename Store<PREC>::T* __restrict__ gpsi = nullptr)
 {
     using L = Lat<LAT>;
     using SP = Store<PREC>;
@@ -553,9 +602,43 @@ __device__ __forceinline__ void fill_one(const KParams& P, typename Store<PREC>:
     T r[Q], d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) SP::load(a, i * np + xp, (Q + i) * np + xp, ph, L::cls(i), r[i], d[i]);
+    // Every direction is stored through put, in index order.  With a ghost-psi table (D3Q19,
+    // whose opposite directions are the consecutive pairs (1, 2) .. (17, 18)) the stored values
+    // are decoded as a later load would decode them and summed in the order of ghost_psi_from
+    // (rest, then each pair), so the table holds the bits ghost_psi would compute.
+    static_assert(LAT != 1 || (L::rep(0) == 1 && L::opp(1) == 2 && L::rep(8) == 17 && L::opp(17) == 18),
+                  "D3Q19 opposite pairs must be consecutive");
+    T sr = 0, sd = 0, hr = 0, hd = 0;
+    auto put = [&](int i, int c, T vr, T vd) {
+        typename SP::S fr, fd;
+        SP::encode(vr, vd, ph, c, fr, fd);
+        a[i * np + g] = fr;
+        a[(Q + i) * np + g] = fd;
+        if (LAT == 1 && gpsi) {
+            T er, ed;
+            SP::decode(fr, fd, ph, c, er, ed);
+            if (i == 0) {
+                sr = er;
+                sd = ed;
+            } else if (i & 1) {
+                hr = er;
+                hd = ed;
+            } else {
+                sr += hr + er;
+                sd += hd + ed;
+            }
+        }
+    };
+    auto finish = [&]() {
+        if (LAT == 1 && gpsi) {
+            const T rho = ph.rho0 + sd;
+            gpsi[t] = (sr - (rho - sr)) / rho;
+        }
+    };
     if (kind == LBCG_PORT_ZERO_GRADIENT) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) SP::store(a, i * np + g, (Q + i) * np + g, ph, L::cls(i), r[i], d[i]);
+        for (int i = 0; i < Q; ++i) put(i, L::cls(i), r[i], d[i]);
+        finish();
         return;
     }
     T rr = 0, dr = 0, jx = 0, jy = 0, jz = 0;
@@ -588,7 +671,7 @@ __device__ __forceinline__ void fill_one(const KParams& P, typename Store<PREC>:
             const T neq = d[i] - (wi * dr + rr * ph.dphiR[c] + rb * ph.dphiB[c] + wi * rho * pu);
             const T gr = xr * rho * (ph.phiR[c] + wi * pv) + xr * neq;
             const T gd = wi * dr + xr * rho * ph.dphiR[c] + xb * rho * ph.dphiB[c] + wi * rho * pv + neq;
-            SP::store(a, i * np + g, (Q + i) * np + g, ph, c, gr, gd);
+            put(i, c, gr, gd);
         }
     } else {
         const T fac = (T)gu[3 * ng + t] * inv_rho - T(1);
@@ -599,9 +682,10 @@ __device__ __forceinline__ void fill_one(const KParams& P, typename Store<PREC>:
             const T cu = (T)L::cx(i) * ux + (T)L::cy(i) * uy + (T)L::cz(i) * uz;
             const T pu = wi * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq);
             const T er = rr * (ph.phiR[c] + pu), eb = rb * (ph.phiB[c] + pu);
-            SP::store(a, i * np + g, (Q + i) * np + g, ph, c, r[i] + fac * er, d[i] + fac * (er + eb));
+            put(i, c, r[i] + fac * er, d[i] + fac * (er + eb));
         }
     }
+    finish();  // the ghost's psi for the next step's colour gradient
 }
 
 }  // namespace lbcg

@@ -118,28 +118,6 @@ __device__ __forceinline__ typename Store<PREC>::T pull_fluid(const KParams& P,
     return (rr - (rho - rr)) / rho;
 }
 
-// psi of a port ghost site from its own (already filled) populations
-template <int LAT, int PREC, typename IDX>
-__device__ __forceinline__ typename Store<PREC>::T ghost_psi(const KParams& P,
-                                                             const typename Store<PREC>::S* __restrict__ A, IDX s)
-{
-    using L = Lat<LAT>;
-    using SP = Store<PREC>;
-    using T = typename SP::T;
-    const IDX np = (IDX)P.np;
-    T rr = 0, sg = 0;
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        T r, g;
-        const IDX ir = (IDX)i * np + s;
-        load_pop<PREC, IDX>(P, A, ir, ir + (IDX)L::Q * np, phys<T>(P), L::cls(i), r, g);
-        rr += r;
-        sg += g;
-    }
-    const T rho = phys<T>(P).rho0 + sg;
-    return (rr - (rho - rr)) / rho;
-}
-
 template <int LAT, int PREC, typename IDX>
 __device__ __forceinline__ void store_site(const KParams& P, typename Store<PREC>::S* __restrict__ B, IDX s,
                                            const typename Store<PREC>::T (&r)[Lat<LAT>::Q],
@@ -446,6 +424,12 @@ __global__ void __launch_bounds__(256, 3) k_step_d3q19_occ(const KParams P,
 // the output buffer from the populations of x' its threads have just written there (fill_one,
 // the rule of the separate refill, one thread per ghost), so the next step finds them
 // refilled without a refill launch.
+//
+// Ghost-psi table: the refill also stores each ghost's psi (computed from the values it has
+// just written, in compute precision) in a per-buffer table, and the link word of a port site
+// carries its ghost-table row.  A port lane of the march then reads one value instead of
+// pulling the ghost's 2Q populations in a branch of its own, which the fluid lanes of the same
+// warp would wait through.
 
 struct PortTab {
     const int* tab;     // ghost table [4][ng] (site, inward neighbour, port, kind) or nullptr
@@ -453,7 +437,23 @@ struct PortTab {
     int ng;
     const int* gstart;  // [ntiles + 1] first row in grow of each tile
     const int* grow;    // ghost-table rows grouped by tile
+    const void* gpsi_in;  // ghost-psi table of the input buffer (compute type) or nullptr
+    void* gpsi_out;       // of the output buffer, written by the refill, or nullptr
 };
+
+// psi of the port site s (link word lk) from the input buffer's ghost-psi table, else from
+// the ghost's populations
+template <int PREC, typename IDX>
+__device__ __forceinline__ typename Store<PREC>::T port_psi(const KParams& P,
+                                                            const typename Store<PREC>::S* __restrict__ A, IDX s,
+                                                            uint32_t lk, const typename Store<PREC>::T* gpsi, int ng)
+{
+    if (gpsi) {
+        const int t = (int)(lk & kGhostMask);
+        if (in_bounds(P, t, ng)) return gpsi[t];
+    }
+    return ghost_psi<1, PREC, IDX>(P, A, s);
+}
 
 template <int PREC>
 __device__ __forceinline__ void refill_tile_ports(const KParams& P, typename Store<PREC>::S* B, const PortTab& pt,
@@ -464,7 +464,7 @@ __device__ __forceinline__ void refill_tile_ports(const KParams& P, typename Sto
     __syncthreads();       // the populations of every x' of the tile are written
     const int nt = blockDim.x * blockDim.y;
     for (int e = g0 + threadIdx.y * blockDim.x + threadIdx.x; e < g1; e += nt)
-        fill_one<1, PREC>(P, B, pt.tab, pt.gu, pt.ng, pt.grow[e]);
+        fill_one<1, PREC>(P, B, pt.tab, pt.gu, pt.ng, pt.grow[e], (typename Store<PREC>::T*)pt.gpsi_out);
 }
 
 // ---------------------------------------------------------- neighbour-only plane barrier
@@ -561,7 +561,9 @@ __device__ __forceinline__ typename Store<PREC>::T pull_moments(const KParams& P
             mom_add_pair<LAT, FULL>(m, k, rp, gp, rq, gq);
         }
     };
-    if ((lk & qmask) == 0u)
+    // one body per warp: the bounce-back body is right for every site, so a warp with any
+    // bounced link takes it for all its lanes instead of running both bodies one after the other
+    if (!__any_sync(__activemask(), (lk & qmask) != 0u))
         body(std::false_type{});
     else
         body(std::true_type{});
@@ -580,7 +582,8 @@ template <int PREC, typename IDX, bool MSMEM, bool PAIR = false>
 __device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename Store<PREC>::S* __restrict__ A,
                                                typename Store<PREC>::S* __restrict__ B,
                                                const uint32_t* __restrict__ link, int bx, int by, int z0, int z1,
-                                               typename Store<PREC>::T* psi_s)
+                                               typename Store<PREC>::T* psi_s,
+                                               const typename Store<PREC>::T* __restrict__ gpsi_in, int gpsi_n)
 {
     using T = typename Store<PREC>::T;
     using SP = Store<PREC>;
@@ -641,7 +644,7 @@ __device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename 
                              : pull_moments<1, PREC, IDX, false>(P, A, s, u, lk, mn);
                 fluid_n = true;
             } else if (type == kTypePort) {
-                psi_n = ghost_psi<1, PREC, IDX>(P, A, s);
+                psi_n = port_psi<PREC, IDX>(P, A, s, lk, gpsi_in, gpsi_n);
             }
         }
         const int slot_n = (zz - z0 + 1) & 3;
@@ -694,7 +697,8 @@ __global__ void __launch_bounds__(256, PREC == LBCG_FP64 ? 2 : 3) k_step_d3q19_m
     extern __shared__ unsigned char smem_raw[];
     int bx, by, z0, z1;
     block_of(P, tiles, bx, by, z0, z1);
-    tile_d3q19_mom<PREC, IDX, false>(P, A, B, link, bx, by, z0, z1, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+    tile_d3q19_mom<PREC, IDX, false>(P, A, B, link, bx, by, z0, z1, reinterpret_cast<typename Store<PREC>::T*>(smem_raw),
+                                     (const typename Store<PREC>::T*)pt.gpsi_in, pt.ng);
     if (pt.tab) refill_tile_ports<PREC>(P, B, pt, (int)blockIdx.x);
 }
 
@@ -710,7 +714,8 @@ __global__ void __launch_bounds__(256, PREC == LBCG_FP64 ? 2 : 3) k_step_d3q19_m
     int bx, by, z0, z1;
     block_of(P, tiles, bx, by, z0, z1);
     tile_d3q19_mom<PREC, IDX, false, true>(P, A, B, link, bx, by, z0, z1,
-                                           reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+                                           reinterpret_cast<typename Store<PREC>::T*>(smem_raw),
+                                           (const typename Store<PREC>::T*)pt.gpsi_in, pt.ng);
     if (pt.tab) refill_tile_ports<PREC>(P, B, pt, (int)blockIdx.x);
 }
 
@@ -726,7 +731,8 @@ __global__ void __launch_bounds__(512, 2) k_step_d3q19_moms(const KParams P,
     extern __shared__ unsigned char smem_raw[];
     int bx, by, z0, z1;
     block_of(P, tiles, bx, by, z0, z1);
-    tile_d3q19_mom<PREC, IDX, true>(P, A, B, link, bx, by, z0, z1, reinterpret_cast<typename Store<PREC>::T*>(smem_raw));
+    tile_d3q19_mom<PREC, IDX, true>(P, A, B, link, bx, by, z0, z1, reinterpret_cast<typename Store<PREC>::T*>(smem_raw),
+                                    (const typename Store<PREC>::T*)pt.gpsi_in, pt.ng);
     if (pt.tab) refill_tile_ports<PREC>(P, B, pt, (int)blockIdx.x);
 }
 
@@ -976,7 +982,8 @@ __device__ __forceinline__ void tile_d3q19_tma(const KParams& P, const CUtensorM
                                                const typename Store<PREC>::S* __restrict__ A,
                                                typename Store<PREC>::S* __restrict__ B,
                                                const uint32_t* __restrict__ link, int bx, int by, int z0, int z1,
-                                               unsigned char* smem, int* status)
+                                               unsigned char* smem, int* status, const float* __restrict__ gpsi_in,
+                                               int gpsi_n)
 {
     using T = float;
     using SP = Store<PREC>;
@@ -1074,7 +1081,7 @@ __device__ __forceinline__ void tile_d3q19_tma(const KParams& P, const CUtensorM
                              : pull_staged<PREC, WY, false>(P, box, A, s, u, lk, edge, x, y, sh, boff, mn);
                 fluid_n = true;
             } else if (type == kTypePort) {
-                psi_n = ghost_psi<1, PREC, int>(P, A, s);
+                psi_n = port_psi<PREC, int>(P, A, s, lk, gpsi_in, gpsi_n);
             }
         }
         ring_put(P, psi_s, (((k & 3) * WY) + w) * 32 + lane, psi_n);
@@ -1138,12 +1145,14 @@ __global__ void __launch_bounds__(32 * WY, WY <= 6 ? 3 : 2) k_step_d3q19_tma(con
                                                                               const typename Store<PREC>::S* __restrict__ A,
                                                                               typename Store<PREC>::S* __restrict__ B,
                                                                               const uint32_t* __restrict__ link,
-                                                                              const int* __restrict__ tiles, int* status)
+                                                                              const int* __restrict__ tiles, int* status,
+                                                                              const float* __restrict__ gpsi_in,
+                                                                              int gpsi_n)
 {
     extern __shared__ __align__(1024) unsigned char smem_tma[];
     int bx, by, z0, z1;
     block_of(P, tiles, bx, by, z0, z1);
-    tile_d3q19_tma<PREC, WY>(P, &tmA, A, B, link, bx, by, z0, z1, smem_tma, status);
+    tile_d3q19_tma<PREC, WY>(P, &tmA, A, B, link, bx, by, z0, z1, smem_tma, status, gpsi_in, gpsi_n);
 }
 
 // ------------------------------------------------------------- batched kernels
@@ -1210,7 +1219,8 @@ __global__ void __launch_bounds__(256, MINB) k_batch_d3q19(const BatchSlot* __re
         const S* src = (const S*)(odd ? sl.b : sl.a);
         S* dst = (S*)(odd ? sl.a : sl.b);
         if (sP.collision == LBCG_REG)
-            tile_d3q19_mom<PREC, int, false>(sP, src, dst, sl.link, it.x, it.y, it.z & 0xffff, it.z >> 16, reinterpret_cast<T*>(smem_raw));
+            tile_d3q19_mom<PREC, int, false>(sP, src, dst, sl.link, it.x, it.y, it.z & 0xffff, it.z >> 16,
+                                             reinterpret_cast<T*>(smem_raw), nullptr, 0);
         else
             tile_d3q19<PREC, false, int>(sP, src, dst, sl.link, it.x, it.y, it.z & 0xffff, it.z >> 16, reinterpret_cast<T*>(smem_raw));
     }
@@ -1355,9 +1365,11 @@ static cudaError_t launch_d3q19_tma(lbcg_ctx* c, const void* a, void* b)
     const int* tl = c->d_tiles;
     const dim3 grid = tl ? dim3((unsigned)P.ntiles) : dim3(P.nsx, P.nsy, P.nsz);
     const uint32_t* lk = c->any_link ? c->d_link : nullptr;
+    const float* gp = (const float*)gpsi_for(c, a);
     auto go = [&](auto kern, int bytes, int rows) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        kern<<<grid, dim3(32, rows), (size_t)bytes, c->stream>>>(P, *m, (const S*)a, (S*)b, lk, tl, c->d_status);
+        kern<<<grid, dim3(32, rows), (size_t)bytes, c->stream>>>(P, *m, (const S*)a, (S*)b, lk, tl, c->d_status, gp,
+                                                                   c->nghost);
     };
     if (wy == 8)
         go(k_step_d3q19_tma<PREC, 8>, TmaLayout<8>::BYTES, 8);
@@ -1379,7 +1391,8 @@ static cudaError_t launch_d3q19(lbcg_ctx* c, const void* a, void* b, int variant
     size_t smem = 4 * (size_t)wy * 32 * sizeof(T);
     const uint32_t* lk = c->any_link ? c->d_link : nullptr;
     const bool fuse = c->nghost > 0 && c->d_gstart && tl;
-    const PortTab pt{fuse ? c->d_ghost : nullptr, c->d_ghost_u, c->nghost, c->d_gstart, c->d_grow};
+    const PortTab pt{fuse ? c->d_ghost : nullptr, c->d_ghost_u, c->nghost, c->d_gstart, c->d_grow,
+                     gpsi_for(c, a), fuse ? gpsi_for(c, b) : nullptr};
     if (variant == 7 && !KEEP) {
         const size_t smem7 = smem + 2 * 11 * (size_t)wy * 32 * sizeof(T);
         auto go = [&](auto kern) {
