@@ -359,6 +359,31 @@ def test_ported_step_emulsifier_1000_steps(shape):
     assert relmax(gu, ou) <= 1e-5, relmax(gu, ou)
 
 
+# Switching the step kernel mid-run on a ported box: the marches (6, 7, 9) refill the ghosts and
+# the ghost-psi table of the state they write, the TMA march (8) and the re-read kernels (5, 2)
+# run the refill launch first (which also writes the table) unless the ghosts are fresh, and the
+# port lanes of the marches read the table of their input.  Every order of these keeps the FP64
+# run on the oracle, and the FP32-dev run (8 included) within its tolerance of it.
+def test_variant_switches_mid_run_ported():
+    lb = _lb()
+    pb = W.step_emulsifier(nx=64, ny=30, nz=12, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10)
+    o = oracle.Sim(pb)
+    o.step(240)
+    orr, ob, ou = o.fields()
+    plan = [(6, 8, 8, 30), (9, 8, 8, 30), (5, 8, 8, 20), (7, 6, 4, 30), (6, 8, 8, 1), (2, 5, 7, 19),
+            (9, 4, 5, 30), (8, 8, 8, 30), (6, 8, 8, 50)]
+    g64 = lb.Simulation(pb, lb.LBCG_FP64)
+    g32 = lb.Simulation(pb, lb.LBCG_FP32_DEV)
+    for v, b, r, n in plan:
+        for g in (g64, g32):
+            g.set_launch(rows=r, block_rows=b, variant=v)
+            g.step(n)
+    assert g64.step_count == 240
+    assert pops_diff(g64.populations(), o.populations(), pb) <= 1e-11
+    gr, gb, gu = g32.fields()
+    assert relmax(gr, orr) <= 1e-5 and relmax(gb, ob) <= 1e-5 and relmax(gu, ou) <= 1e-5
+
+
 # ------------------------------------------------------------ observables, labels
 
 def test_observables_match_oracle():
