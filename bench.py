@@ -378,7 +378,7 @@ def fp64_sample(lbcg, pb, stream, fluid: int, workload: str, steps: int = 20) ->
 
 def roofline_2d_sample(lbcg, stream, steps: int = 20) -> dict:
     """The 4096^2 D2Q9 droplet (state far larger than L2), FP32-dev, library default launch
-    shape: the 2D roofline instance, kernel time of `steps` individual launches."""
+    shape: the 2D roofline instance, kernel time over `steps` consecutive launches."""
     pb, desc, _ = W.named("droplet2d")
     sim = lbcg.Simulation(pb, PREC["f32dev"], stream=stream)
     k_avg, whole_ms = _kernel_timed(sim, steps, stream)

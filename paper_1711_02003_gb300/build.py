@@ -20,14 +20,15 @@ LIB = os.path.join(HERE, "liblbcg.so")
 # index of the step kernels checked, violations reported as LBCG_ERR_BOUNDS
 BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(HERE, "liblbcg_checked.so")
-SOURCES = ["step.cu", "aux.cu", "api.cu", "noalloc.cu", "batch.cu", "peak.cu"]
+SOURCES = ["step.cu", "step_f64.cu", "step_f32.cu", "step_f32dev.cu", "step_f16.cu", "aux.cu", "api.cu", "noalloc.cu",
+           "batch.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
            "-Xptxas", "-warn-spills"]
 
 
 # sources that define the fused step kernels (a change invalidates recorded ncu counters)
-STEP_KERNEL_SOURCES = ["step.cu", "lbcg_device.cuh", "lbcg_internal.h"]
+STEP_KERNEL_SOURCES = ["step.cu", "step_kernels.cuh", "lbcg_device.cuh", "lbcg_internal.h"]
 
 
 def step_kernel_digest() -> str:

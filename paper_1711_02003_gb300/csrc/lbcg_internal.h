@@ -179,6 +179,18 @@ namespace lbcg {
 
 // launchers (step.cu)
 cudaError_t launch_step(lbcg_ctx* c, const void* a, void* b);
+// the same for one storage format (step_kernels.cuh, one translation unit per format)
+template <int PREC>
+cudaError_t launch_step_prec(lbcg_ctx* c, const void* a, void* b);
+template <int PREC>
+int batch_resident_blocks_prec(int lattice, int wy);
+template <int PREC>
+cudaError_t launch_batch_step_prec(int lattice, const BatchSlot* slots, const BatchItem* items, const int* nitems,
+                                   int k, int grid, int wy, cudaStream_t st);
+// 32-bit element offsets suffice: all 2Q planes of the state below 2^31 elements
+inline bool small_index(const lbcg_ctx* c) { return (long long)2 * c->Q * (long long)c->np < (1LL << 31) - 1; }
+// cuTensorMapEncodeTiled from the driver (nullptr where unavailable), as a plain pointer (step.cu)
+void* tma_encode_entry();
 // ghost-psi table of state buffer `buf` (compute type), or nullptr without a table (api.cu)
 void* gpsi_for(lbcg_ctx* c, const void* buf);
 int effective_variant(const lbcg_ctx* c);  // the step kernel variant launch_step runs
