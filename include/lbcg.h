@@ -347,8 +347,9 @@ int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
  * the environment variable LBCG_TEST_PIPELINE_STALL=1 is set makes every pipeline wait of
  * variant 8 run out (failure-path test): the step then leaves the state invalid and
  * lbcg_synchronize and the read-back calls report LBCG_ERR_TIMEOUT once.  The default is the
- * moment march (6) for the regularized collision on either lattice; with BGK the plain
- * march for D2Q9 and variant 5 (FP64: 2) for D3Q19.  D2Q9 takes 6 (moment march,
+ * moment march for the regularized collision on either lattice (D3Q19 boxes with walls or
+ * ports: 9, up to 8 warps per block; otherwise 6); with BGK the plain march for D2Q9 and
+ * variant 5 (FP64: 2) for D3Q19.  D2Q9 takes 6 (moment march,
  * regularized only) and treats every other value as the plain march.  Values 3, 4 and
  * above 9 are rejected (LBCG_ERR_ARG).
  * Within one variant results are bit-identical across shapes; variants may contract

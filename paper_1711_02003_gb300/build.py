@@ -28,7 +28,8 @@ NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-rela
 
 
 # sources that define the fused step kernels (a change invalidates recorded ncu counters)
-STEP_KERNEL_SOURCES = ["step.cu", "step_kernels.cuh", "lbcg_device.cuh", "lbcg_internal.h"]
+# the sources of the step kernels' device code (step.cu holds host-side dispatch only)
+STEP_KERNEL_SOURCES = ["step_kernels.cuh", "lbcg_device.cuh", "lbcg_internal.h"]
 
 
 def step_kernel_digest() -> str:

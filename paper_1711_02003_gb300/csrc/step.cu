@@ -45,10 +45,13 @@ int effective_variant(const lbcg_ctx* c)
     if (c->p.lattice == LBCG_D2Q9) {
         return (c->variant == 0 || c->variant == 6) && c->p.collision == LBCG_REG ? 6 : 0;
     }
-    // default (measured fastest): the moment march with its moments in registers; the BGK
-    // update needs the individual populations and re-reads them (three blocks per SM, FP64 two)
+    // default (measured fastest): the moment march with its moments in registers, on boxes with
+    // walls or ports with neighbour-only plane barriers (9; on a link-free periodic box the two
+    // run alike); the BGK update needs the individual populations and re-reads them (three
+    // blocks per SM, FP64 two)
     const bool reg = c->p.collision == LBCG_REG;
-    int v = c->variant != 0 ? c->variant : (reg ? 6 : (prec == LBCG_FP64 ? 2 : 5));
+    const int dflt = reg ? (c->any_link && c->block_rows <= 8 ? 9 : 6) : (prec == LBCG_FP64 ? 2 : 5);
+    int v = c->variant != 0 ? c->variant : dflt;
     if (v == 8 && !tma_supported(c)) v = prec == LBCG_FP64 ? 6 : 7;
     if ((v == 6 || v == 7 || v == 9) && !reg) v = prec == LBCG_FP64 ? 2 : 5;
     return v;
