@@ -87,7 +87,9 @@ __global__ void __launch_bounds__(kFillThreads) k_batch_fill(const BatchSlot* __
     if (k >= sl.steps) return;
     if ((int)threadIdx.x >= it.y) return;
     typename Store<PREC>::S* src = (typename Store<PREC>::S*)((k & 1) ? sl.b : sl.a);
-    fill_one<LAT, PREC>(sl.kp, src, sl.ghost, sl.ghost_u, sl.nghost, it.x + (int)threadIdx.x);
+    // the source buffer's ghost-psi table too (D3Q19), read by the batched march's port lanes
+    fill_one<LAT, PREC>(sl.kp, src, sl.ghost, sl.ghost_u, sl.nghost, it.x + (int)threadIdx.x,
+                        (typename Store<PREC>::T*)((k & 1) ? sl.gpsi_b : sl.gpsi_a));
 }
 
 // ---------------------------------------------------------------- initial state

@@ -354,6 +354,8 @@ int lbcg_batch_step(lbcg_batch* b, long long max_steps)
             h.ghost = c->d_ghost;
             h.ghost_u = c->d_ghost_u;
             h.nghost = c->nghost;
+            h.gpsi_a = gpsi_for(c, c->A);
+            h.gpsi_b = gpsi_for(c, c->B);
             h.steps = (int)std::min<long long>(chunk, b->remaining[s]);
         }
         e = cudaMemcpyAsync(b->d_slots, tab, sizeof(BatchSlot) * b->max_slots, cudaMemcpyHostToDevice, b->stream);

@@ -79,6 +79,8 @@ struct BatchSlot {
     const int* ghost;        // port ghost table or nullptr
     const double* ghost_u;
     int nghost;
+    void* gpsi_a;            // ghost-psi tables (compute type) of buffers a and b, or nullptr
+    void* gpsi_b;
     int steps;               // steps this launch advances the instance (0 = idle)
 };
 // work item: D2Q9 (slot, first strip, strip count <= 8, -); D3Q19 (slot, bx, by, z0 | z1 << 16)

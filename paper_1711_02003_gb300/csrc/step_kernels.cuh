@@ -1224,7 +1224,8 @@ __global__ void __launch_bounds__(256, MINB) k_batch_d3q19(const BatchSlot* __re
         S* dst = (S*)(odd ? sl.a : sl.b);
         if (sP.collision == LBCG_REG)
             tile_d3q19_mom<PREC, int, false>(sP, src, dst, sl.link, it.x, it.y, it.z & 0xffff, it.z >> 16,
-                                             reinterpret_cast<T*>(smem_raw), nullptr, 0);
+                                             reinterpret_cast<T*>(smem_raw),
+                                             (const T*)(odd ? sl.gpsi_b : sl.gpsi_a), sl.nghost);
         else
             tile_d3q19<PREC, false, int>(sP, src, dst, sl.link, it.x, it.y, it.z & 0xffff, it.z >> 16, reinterpret_cast<T*>(smem_raw));
     }
