@@ -537,8 +537,8 @@ int lbcg_set_geometry(lbcg_ctx* c, const uint8_t* mask, const lbcg_port* ports, 
     }
     // ghost table: [site | inward neighbour | port | kind] and [ux | uy | uz | rho | psi]
     const int ng = (int)ghosts.size();
-    // D3Q19: the port site's link word carries its ghost-table row (the ghost-psi table)
-    const bool gpsi = c->p.lattice == LBCG_D3Q19 && ng > 0 && (long long)ng <= (long long)kGhostMask + 1;
+    // the port site's link word carries its ghost-table row (the ghost-psi table)
+    const bool gpsi = ng > 0 && (long long)ng <= (long long)kGhostMask + 1;
     if (gpsi)
         for (int t = 0; t < ng; ++t) link[(size_t)ghosts[t]] |= (uint32_t)t;
     std::vector<int> tab((size_t)4 * std::max(ng, 1));

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kFillThreads) k_batch_fill(const BatchSlot* __
     if (k >= sl.steps) return;
     if ((int)threadIdx.x >= it.y) return;
     typename Store<PREC>::S* src = (typename Store<PREC>::S*)((k & 1) ? sl.b : sl.a);
-    // the source buffer's ghost-psi table too (D3Q19), read by the batched march's port lanes
+    // the source buffer's ghost-psi table too, read by the batched march's port lanes
     fill_one<LAT, PREC>(sl.kp, src, sl.ghost, sl.ghost_u, sl.nghost, it.x + (int)threadIdx.x,
                         (typename Store<PREC>::T*)((k & 1) ? sl.gpsi_b : sl.gpsi_a));
 }
@@ -288,8 +288,8 @@ cudaError_t launch_fill_ports(lbcg_ctx* c, void* a)
 {
     if (c->nghost == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((c->nghost + kFillThreads - 1) / kFillThreads);  // a thread per ghost
-    // the ghost-psi table of buffer a (D3Q19 with a table), read by the marches' port lanes
-    void* gpsi = c->p.lattice == LBCG_D3Q19 ? gpsi_for(c, a) : nullptr;
+    // the ghost-psi table of buffer a, read by the marches' port lanes
+    void* gpsi = gpsi_for(c, a);
 #define F_(LAT, PREC)                                                                                   \
     k_fill_ports<LAT, PREC><<<blocks, kFillThreads, 0, c->stream>>>(c->kp, (SOf<PREC>*)a, c->d_ghost, \
                                                                     c->d_ghost_u, c->nghost,          \

@@ -602,38 +602,49 @@ __device__ __forceinline__ void fill_one(const KParams& P, typename Store<PREC>:
     T r[Q], d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) SP::load(a, i * np + xp, (Q + i) * np + xp, ph, L::cls(i), r[i], d[i]);
-    // Every direction is stored through put, in index order.  With a ghost-psi table (D3Q19,
-    // whose opposite directions are the consecutive pairs (1, 2) .. (17, 18)) the stored values
-    // are decoded as a later load would decode them and summed in the order of ghost_psi_from
-    // (rest, then each pair), so the table holds the bits ghost_psi would compute.
+    // Every direction is stored through put, in index order.  With a ghost-psi table the stored
+    // values are decoded as a later load would decode them and summed in the order of
+    // ghost_psi_from (rest, then each opposite pair), so the table holds the bits ghost_psi would
+    // compute.  D3Q19, whose opposite directions are the consecutive pairs (1, 2) .. (17, 18),
+    // sums as it stores (the fused refill runs inside the register budget of the march); D2Q9,
+    // refilled by separate kernels only, keeps the decoded values and sums them at the end.
     static_assert(LAT != 1 || (L::rep(0) == 1 && L::opp(1) == 2 && L::rep(8) == 17 && L::opp(17) == 18),
                   "D3Q19 opposite pairs must be consecutive");
     T sr = 0, sd = 0, hr = 0, hd = 0;
+    T kr[LAT == 0 ? Q : 1], kd[LAT == 0 ? Q : 1];
     auto put = [&](int i, int c, T vr, T vd) {
         typename SP::S fr, fd;
         SP::encode(vr, vd, ph, c, fr, fd);
         a[i * np + g] = fr;
         a[(Q + i) * np + g] = fd;
-        if (LAT == 1 && gpsi) {
-            T er, ed;
-            SP::decode(fr, fd, ph, c, er, ed);
-            if (i == 0) {
-                sr = er;
-                sd = ed;
-            } else if (i & 1) {
-                hr = er;
-                hd = ed;
-            } else {
-                sr += hr + er;
-                sd += hd + ed;
-            }
+        if (!gpsi) return;
+        T er, ed;
+        SP::decode(fr, fd, ph, c, er, ed);
+        if (LAT == 0) {
+            kr[LAT == 0 ? i : 0] = er;
+            kd[LAT == 0 ? i : 0] = ed;
+        } else if (i == 0) {
+            sr = er;
+            sd = ed;
+        } else if (i & 1) {
+            hr = er;
+            hd = ed;
+        } else {
+            sr += hr + er;
+            sd += hd + ed;
         }
     };
     auto finish = [&]() {
-        if (LAT == 1 && gpsi) {
-            const T rho = ph.rho0 + sd;
-            gpsi[t] = (sr - (rho - sr)) / rho;
+        if (!gpsi) return;
+        if (LAT == 0) {
+            gpsi[t] = ghost_psi_from<LAT, T>(ph, [&](int i, T& r, T& d) {
+                r = kr[LAT == 0 ? i : 0];
+                d = kd[LAT == 0 ? i : 0];
+            });
+            return;
         }
+        const T rho = ph.rho0 + sd;
+        gpsi[t] = (sr - (rho - sr)) / rho;
     };
     if (kind == LBCG_PORT_ZERO_GRADIENT) {
 #pragma unroll

@@ -27,8 +27,8 @@ struct TraceRange {
 // type (0 fluid, 1 wall, 2 port ghost).
 constexpr uint32_t kTypeShift = 24;
 constexpr uint32_t kTypeFluid = 0, kTypeWall = 1, kTypePort = 2;
-// D3Q19 port sites: bits 0..23 of the link word hold the site's ghost-table row (when the
-// context keeps a ghost-psi table; at most kGhostMask + 1 ghosts)
+// port sites: bits 0..23 of the link word hold the site's ghost-table row (when the context
+// keeps a ghost-psi table; at most kGhostMask + 1 ghosts)
 constexpr uint32_t kGhostMask = (1u << 24) - 1u;
 
 // Physical constants in the arithmetic type of a kernel (float or double), so FP32
@@ -136,7 +136,7 @@ struct lbcg_ctx {
     // the port ghosts of state A already hold the refill from A (written by a step kernel
     // that refills ports itself), so that kernel may run without a refill launch before it
     bool ghosts_fresh = false;
-    // D3Q19 with ports: psi of every ghost, one table of nghost values (compute type, 8-byte
+    // boxes with ports: psi of every ghost, one table of nghost values (compute type, 8-byte
     // slots) per state buffer; gpsi_buf[k] is the buffer table k belongs to.  Written by every
     // refill of that buffer's ghosts, read by the moment marches' port lanes
     double* d_gpsi = nullptr;

@@ -184,12 +184,27 @@ __device__ __forceinline__ T ring_get(const KParams& P, const T* ring, int i)
     return in_bounds(P, i, 4LL * blockDim.x * blockDim.y) ? ring[i] : T(0);
 }
 
+// psi of the port site s (link word lk) from the input buffer's ghost-psi table, else from
+// the ghost's populations
+template <int LAT, int PREC, typename IDX>
+__device__ __forceinline__ typename Store<PREC>::T port_psi(const KParams& P,
+                                                            const typename Store<PREC>::S* __restrict__ A, IDX s,
+                                                            uint32_t lk, const typename Store<PREC>::T* gpsi, int ng)
+{
+    if (gpsi) {
+        const int t = (int)(lk & kGhostMask);
+        if (in_bounds(P, t, ng)) return gpsi[t];
+    }
+    return ghost_psi<LAT, PREC, IDX>(P, A, s);
+}
+
 // ------------------------------------------------------------------------ D2Q9
 // one warp: the strip (sxi, syi) of 30 x rows sites
 template <int PREC, typename IDX>
 __device__ __forceinline__ void strip_d2q9(const KParams& P, const typename Store<PREC>::S* __restrict__ A,
                                            typename Store<PREC>::S* __restrict__ B, const uint32_t* __restrict__ link,
-                                           int sxi, int syi)
+                                           int sxi, int syi, const typename Store<PREC>::T* __restrict__ gpsi_in,
+                                           int gpsi_n)
 {
     using T = typename Store<PREC>::T;
     using L = Lat<0>;
@@ -233,7 +248,7 @@ __device__ __forceinline__ void strip_d2q9(const KParams& P, const typename Stor
                 psi_n = pull_fluid<0, PREC, IDX>(P, A, s, u, lk, rn, gn);
                 fluid_n = true;
             } else if (type == kTypePort) {
-                psi_n = ghost_psi<0, PREC, IDX>(P, A, s);
+                psi_n = port_psi<0, PREC, IDX>(P, A, s, lk, gpsi_in, gpsi_n);
             }
         }
         if (yy - 1 >= y0) {  // warp-uniform: collide row yy-1
@@ -277,12 +292,13 @@ __device__ __forceinline__ void strip_d2q9(const KParams& P, const typename Stor
 template <int PREC, typename IDX>
 __global__ void __launch_bounds__(256) k_step_d2q9(const KParams P, const typename Store<PREC>::S* __restrict__ A,
                                                    typename Store<PREC>::S* __restrict__ B,
-                                                   const uint32_t* __restrict__ link, const int* __restrict__ tiles)
+                                                   const uint32_t* __restrict__ link, const int* __restrict__ tiles,
+                                                   const typename Store<PREC>::T* __restrict__ gpsi_in, int gpsi_n)
 {
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     int sxi, syi;
     if (!strip_of(P, tiles, gw, sxi, syi)) return;  // warp-uniform
-    strip_d2q9<PREC, IDX>(P, A, B, link, sxi, syi);
+    strip_d2q9<PREC, IDX>(P, A, B, link, sxi, syi, gpsi_in, gpsi_n);
 }
 
 // ----------------------------------------------------------------------- D3Q19
@@ -442,20 +458,6 @@ struct PortTab {
     const void* gpsi_in;  // ghost-psi table of the input buffer (compute type) or nullptr
     void* gpsi_out;       // of the output buffer, written by the refill, or nullptr
 };
-
-// psi of the port site s (link word lk) from the input buffer's ghost-psi table, else from
-// the ghost's populations
-template <int PREC, typename IDX>
-__device__ __forceinline__ typename Store<PREC>::T port_psi(const KParams& P,
-                                                            const typename Store<PREC>::S* __restrict__ A, IDX s,
-                                                            uint32_t lk, const typename Store<PREC>::T* gpsi, int ng)
-{
-    if (gpsi) {
-        const int t = (int)(lk & kGhostMask);
-        if (in_bounds(P, t, ng)) return gpsi[t];
-    }
-    return ghost_psi<1, PREC, IDX>(P, A, s);
-}
 
 template <int PREC>
 __device__ __forceinline__ void refill_tile_ports(const KParams& P, typename Store<PREC>::S* B, const PortTab& pt,
@@ -646,7 +648,7 @@ __device__ __forceinline__ void tile_d3q19_mom(const KParams& P, const typename 
                              : pull_moments<1, PREC, IDX, false>(P, A, s, u, lk, mn);
                 fluid_n = true;
             } else if (type == kTypePort) {
-                psi_n = port_psi<PREC, IDX>(P, A, s, lk, gpsi_in, gpsi_n);
+                psi_n = port_psi<1, PREC, IDX>(P, A, s, lk, gpsi_in, gpsi_n);
             }
         }
         const int slot_n = (zz - z0 + 1) & 3;
@@ -746,7 +748,8 @@ __global__ void __launch_bounds__(512, 2) k_step_d3q19_moms(const KParams P,
 template <int PREC, typename IDX>
 __device__ __forceinline__ void strip_d2q9_mom(const KParams& P, const typename Store<PREC>::S* __restrict__ A,
                                                typename Store<PREC>::S* __restrict__ B,
-                                               const uint32_t* __restrict__ link, int sxi, int syi)
+                                               const uint32_t* __restrict__ link, int sxi, int syi,
+                                               const typename Store<PREC>::T* __restrict__ gpsi_in, int gpsi_n)
 {
     using T = typename Store<PREC>::T;
     using SP = Store<PREC>;
@@ -793,7 +796,7 @@ __device__ __forceinline__ void strip_d2q9_mom(const KParams& P, const typename 
                 psi_n = pull_moments<0, PREC, IDX, true>(P, A, s, u, lk, mn);
                 fluid_n = true;
             } else if (type == kTypePort) {
-                psi_n = ghost_psi<0, PREC, IDX>(P, A, s);
+                psi_n = port_psi<0, PREC, IDX>(P, A, s, lk, gpsi_in, gpsi_n);
             }
         }
         if (yy - 1 >= y0) {  // warp-uniform: collide row yy-1
@@ -835,12 +838,13 @@ template <int PREC, typename IDX>
 __global__ void __launch_bounds__(256) k_step_d2q9_mom(const KParams P, const typename Store<PREC>::S* __restrict__ A,
                                                        typename Store<PREC>::S* __restrict__ B,
                                                        const uint32_t* __restrict__ link,
-                                                       const int* __restrict__ tiles)
+                                                       const int* __restrict__ tiles,
+                                                       const typename Store<PREC>::T* __restrict__ gpsi_in, int gpsi_n)
 {
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     int sxi, syi;
     if (!strip_of(P, tiles, gw, sxi, syi)) return;  // warp-uniform
-    strip_d2q9_mom<PREC, IDX>(P, A, B, link, sxi, syi);
+    strip_d2q9_mom<PREC, IDX>(P, A, B, link, sxi, syi, gpsi_in, gpsi_n);
 }
 
 // ------------------------------------------- TMA-staged moment march (variant 8)
@@ -1085,7 +1089,7 @@ __device__ __forceinline__ void tile_d3q19_tma(const KParams& P, const CUtensorM
                              : pull_staged<PREC, WY, false>(P, box, A, s, u, lk, edge, x, y, sh, boff, mn);
                 fluid_n = true;
             } else if (type == kTypePort) {
-                psi_n = port_psi<PREC, int>(P, A, s, lk, gpsi_in, gpsi_n);
+                psi_n = port_psi<1, PREC, int>(P, A, s, lk, gpsi_in, gpsi_n);
             }
         }
         ring_put(P, psi_s, (((k & 3) * WY) + w) * 32 + lane, psi_n);
@@ -1195,7 +1199,8 @@ __global__ void __launch_bounds__(256) k_batch_d2q9(const BatchSlot* __restrict_
         const int wib = threadIdx.x >> 5;
         if (wib < it.y) {
             const int strip = it.x + wib;
-            strip_d2q9<PREC, int>(sP, src, dst, sl.link, strip % sP.nsx, strip / sP.nsx);
+            strip_d2q9<PREC, int>(sP, src, dst, sl.link, strip % sP.nsx, strip / sP.nsx,
+                                  (const typename Store<PREC>::T*)(odd ? sl.gpsi_b : sl.gpsi_a), sl.nghost);
         }
     }
 }
@@ -1243,17 +1248,14 @@ static cudaError_t launch_d2q9(lbcg_ctx* c, const void* a, void* b)
     const int threads = 256;
     const long long blocks = (warps * 32 + threads - 1) / threads;
     const uint32_t* lk = c->any_link ? c->d_link : nullptr;
-    if (effective_variant(c) == 6) {
-        if (small_index(c))
-            k_step_d2q9_mom<PREC, int><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
-        else
-            k_step_d2q9_mom<PREC, long long><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
-        return cudaGetLastError();
-    }
-    if (small_index(c))
-        k_step_d2q9<PREC, int><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+    // the ghost-psi table of the input, written by the refill launch before the step
+    const auto* gp = (const typename Store<PREC>::T*)gpsi_for(c, a);
+    const int ng = c->nghost;
+    auto go = [&](auto kern) { kern<<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl, gp, ng); };
+    if (effective_variant(c) == 6)
+        small_index(c) ? go(k_step_d2q9_mom<PREC, int>) : go(k_step_d2q9_mom<PREC, long long>);
     else
-        k_step_d2q9<PREC, long long><<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl);
+        small_index(c) ? go(k_step_d2q9<PREC, int>) : go(k_step_d2q9<PREC, long long>);
     return cudaGetLastError();
 }
 
