@@ -226,26 +226,12 @@ int build_tiles(lbcg_ctx* c)
     return build_active_tiles(c);
 }
 
-// D3Q19 tiles of list `list` (column, z0 | z1 << 16): for every port ghost the tile that
-// collides its x', as per-tile row lists (gstart, grow) for the fused refill of the moment marches
-static int build_tile_ghosts(lbcg_ctx* c, const std::vector<int>& list)
+// the per-tile row lists (gstart, grow) of the fused port refill from owner[g], the active-tile
+// index whose sites include ghost g's inward neighbour x'
+static int upload_tile_ghosts(lbcg_ctx* c, int nt, const std::vector<int>& owner)
 {
-    const KParams& k = c->kp;
-    const int nx = c->dims[0], ny = c->dims[1], ty = c->block_rows - 2;
-    const int nt = (int)(list.size() / 2);
-    std::vector<std::vector<int>> by_col((size_t)k.nsx * k.nsy);
-    for (int t = 0; t < nt; ++t) by_col[(size_t)list[2 * t]].push_back(t);
-    std::vector<int> owner((size_t)c->nghost, -1), count((size_t)nt + 1, 0);
-    for (int g = 0; g < c->nghost; ++g) {
-        const long long s = c->ghost_xp[(size_t)g];
-        const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
-        for (int t : by_col[(size_t)((x / 30) + (long long)k.nsx * (y / ty))]) {
-            const int z0 = list[2 * t + 1] & 0xffff, z1 = list[2 * t + 1] >> 16;
-            if (z >= z0 && z < z1) owner[(size_t)g] = t;
-        }
-        if (owner[(size_t)g] < 0) return fail(LBCG_ERR_GEOMETRY, "a port's inward neighbour lies in no tile");
-        ++count[(size_t)owner[(size_t)g] + 1];
-    }
+    std::vector<int> count((size_t)nt + 1, 0);
+    for (int g = 0; g < c->nghost; ++g) ++count[(size_t)owner[(size_t)g] + 1];
     for (int t = 0; t < nt; ++t) count[(size_t)t + 1] += count[(size_t)t];
     std::vector<int> rows((size_t)std::max(c->nghost, 1)), fillp(count.begin(), count.end() - 1);
     for (int g = 0; g < c->nghost; ++g) rows[(size_t)fillp[(size_t)owner[(size_t)g]]++] = g;
@@ -256,6 +242,47 @@ static int build_tile_ghosts(lbcg_ctx* c, const std::vector<int>& list)
         cudaMemcpy(c->d_grow, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(LBCG_ERR_CUDA, "tile ghost list copy failed");
     return LBCG_OK;
+}
+
+// D3Q19 tiles of list `list` (column, z0 | z1 << 16): for every port ghost the tile that
+// collides its x', as per-tile row lists (gstart, grow) for the fused refill of the moment marches
+static int build_tile_ghosts(lbcg_ctx* c, const std::vector<int>& list)
+{
+    const KParams& k = c->kp;
+    const int nx = c->dims[0], ny = c->dims[1], ty = c->block_rows - 2;
+    const int nt = (int)(list.size() / 2);
+    std::vector<std::vector<int>> by_col((size_t)k.nsx * k.nsy);
+    for (int t = 0; t < nt; ++t) by_col[(size_t)list[2 * t]].push_back(t);
+    std::vector<int> owner((size_t)c->nghost, -1);
+    for (int g = 0; g < c->nghost; ++g) {
+        const long long s = c->ghost_xp[(size_t)g];
+        const int x = (int)(s % nx), y = (int)((s / nx) % ny), z = (int)(s / ((long long)nx * ny));
+        for (int t : by_col[(size_t)((x / 30) + (long long)k.nsx * (y / ty))]) {
+            const int z0 = list[2 * t + 1] & 0xffff, z1 = list[2 * t + 1] >> 16;
+            if (z >= z0 && z < z1) owner[(size_t)g] = t;
+        }
+        if (owner[(size_t)g] < 0) return fail(LBCG_ERR_GEOMETRY, "a port's inward neighbour lies in no tile");
+    }
+    return upload_tile_ghosts(c, nt, owner);
+}
+
+// D2Q9 strips of list `list` (strip index sx + nsx sy): for every port ghost the strip whose
+// warp collides its x', for the fused refill of the strip marches
+static int build_strip_ghosts(lbcg_ctx* c, const std::vector<int>& list)
+{
+    const KParams& k = c->kp;
+    const int nx = c->dims[0];
+    const int nt = (int)list.size();
+    std::vector<int> index((size_t)k.nsx * k.nsy, -1);
+    for (int t = 0; t < nt; ++t) index[(size_t)list[(size_t)t]] = t;
+    std::vector<int> owner((size_t)c->nghost, -1);
+    for (int g = 0; g < c->nghost; ++g) {
+        const long long s = c->ghost_xp[(size_t)g];
+        const int x = (int)(s % nx), y = (int)(s / nx);
+        owner[(size_t)g] = index[(size_t)((x / 30) + (long long)k.nsx * (y / k.rows))];
+        if (owner[(size_t)g] < 0) return fail(LBCG_ERR_GEOMETRY, "a port's inward neighbour lies in no strip");
+    }
+    return upload_tile_ghosts(c, nt, owner);
 }
 
 static int build_active_tiles(lbcg_ctx* c)
@@ -283,7 +310,7 @@ static int build_active_tiles(lbcg_ctx* c)
         }
         for (long long t = 0; t < ntot; ++t)
             if (on[(size_t)t]) list.push_back((int)t);
-        if ((long long)list.size() == ntot) return LBCG_OK;  // nothing to skip
+        if ((long long)list.size() == ntot && c->nghost == 0) return LBCG_OK;  // nothing to skip
         if (list.empty()) list.push_back(0);
     } else {
         if (!fitted_tiles_3d(c, k, c->block_rows - 2, list)) return fail(LBCG_ERR_GEOMETRY, "nz above 65535 with walls");
@@ -298,7 +325,7 @@ static int build_active_tiles(lbcg_ctx* c)
         return fail(LBCG_ERR_CUDA, "tile list copy failed");
     c->ntiles = (int)(c->p.lattice == LBCG_D2Q9 ? list.size() : list.size() / 2);
     c->kp.ntiles = c->ntiles;
-    if (c->p.lattice == LBCG_D3Q19 && c->nghost > 0) return build_tile_ghosts(c, list);
+    if (c->nghost > 0) return c->p.lattice == LBCG_D3Q19 ? build_tile_ghosts(c, list) : build_strip_ghosts(c, list);
     return LBCG_OK;
 }
 

@@ -57,10 +57,12 @@ int effective_variant(const lbcg_ctx* c)
     return v;
 }
 
-// the step kernel refills the port ghosts of its output itself (the moment marches)
+// the step kernel refills the port ghosts of its output itself (the D3Q19 moment marches and
+// both D2Q9 strip marches)
 bool step_fuses_ports(const lbcg_ctx* c)
 {
-    if (c->p.lattice != LBCG_D3Q19 || c->nghost == 0 || !c->d_gstart || !c->d_tiles) return false;
+    if (c->nghost == 0 || !c->d_gstart || !c->d_tiles) return false;
+    if (c->p.lattice == LBCG_D2Q9) return true;
     const int v = effective_variant(c);
     return v == 6 || v == 7 || v == 9;
 }

@@ -184,6 +184,18 @@ __device__ __forceinline__ T ring_get(const KParams& P, const T* ring, int i)
     return in_bounds(P, i, 4LL * blockDim.x * blockDim.y) ? ring[i] : T(0);
 }
 
+// port tables of a fused refill (D3Q19 tiles, D2Q9 strips) and the ghost-psi tables of the
+// input and output buffers (the refill and its tables are described with refill_tile_ports)
+struct PortTab {
+    const int* tab;     // ghost table [4][ng] (site, inward neighbour, port, kind) or nullptr
+    const double* gu;   // [5][ng] inlet velocity, port density, port psi
+    int ng;
+    const int* gstart;  // [ntiles + 1] first row in grow of each tile
+    const int* grow;    // ghost-table rows grouped by tile
+    const void* gpsi_in;  // ghost-psi table of the input buffer (compute type) or nullptr
+    void* gpsi_out;       // of the output buffer, written by the refill, or nullptr
+};
+
 // psi of the port site s (link word lk) from the input buffer's ghost-psi table, else from
 // the ghost's populations
 template <int LAT, int PREC, typename IDX>
@@ -289,16 +301,32 @@ __device__ __forceinline__ void strip_d2q9(const KParams& P, const typename Stor
     }
 }
 
-template <int PREC, typename IDX>
+// Fused port refill of a D2Q9 strip march: the ghosts whose inward neighbour x' lies in strip
+// `strip` of the active list (rows gstart[strip] .. gstart[strip + 1] - 1 of grow), rebuilt
+// by the warp that has just written every x' of the strip, one lane per ghost
+template <int PREC>
+__device__ __forceinline__ void refill_strip_ports(const KParams& P, typename Store<PREC>::S* B, const PortTab& pt,
+                                                   int strip)
+{
+    const int g0 = pt.gstart[strip], g1 = pt.gstart[strip + 1];
+    if (g0 >= g1) return;  // warp-uniform
+    __syncwarp();          // the populations of every x' of the strip are written
+    for (int e = g0 + (int)(threadIdx.x & 31); e < g1; e += 32)
+        fill_one<0, PREC>(P, B, pt.tab, pt.gu, pt.ng, pt.grow[e], (typename Store<PREC>::T*)pt.gpsi_out);
+}
+
+// PORTS: compiled with the fused port refill (launched for boxes with ports)
+template <int PREC, typename IDX, bool PORTS>
 __global__ void __launch_bounds__(256) k_step_d2q9(const KParams P, const typename Store<PREC>::S* __restrict__ A,
                                                    typename Store<PREC>::S* __restrict__ B,
                                                    const uint32_t* __restrict__ link, const int* __restrict__ tiles,
-                                                   const typename Store<PREC>::T* __restrict__ gpsi_in, int gpsi_n)
+                                                   const PortTab pt)
 {
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     int sxi, syi;
     if (!strip_of(P, tiles, gw, sxi, syi)) return;  // warp-uniform
-    strip_d2q9<PREC, IDX>(P, A, B, link, sxi, syi, gpsi_in, gpsi_n);
+    strip_d2q9<PREC, IDX>(P, A, B, link, sxi, syi, (const typename Store<PREC>::T*)pt.gpsi_in, pt.ng);
+    if (PORTS && pt.tab) refill_strip_ports<PREC>(P, B, pt, gw);
 }
 
 // ----------------------------------------------------------------------- D3Q19
@@ -449,15 +477,6 @@ __global__ void __launch_bounds__(256, 3) k_step_d3q19_occ(const KParams P,
 // pulling the ghost's 2Q populations in a branch of its own, which the fluid lanes of the same
 // warp would wait through.
 
-struct PortTab {
-    const int* tab;     // ghost table [4][ng] (site, inward neighbour, port, kind) or nullptr
-    const double* gu;   // [5][ng] inlet velocity, port density, port psi
-    int ng;
-    const int* gstart;  // [ntiles + 1] first row in grow of each tile
-    const int* grow;    // ghost-table rows grouped by tile
-    const void* gpsi_in;  // ghost-psi table of the input buffer (compute type) or nullptr
-    void* gpsi_out;       // of the output buffer, written by the refill, or nullptr
-};
 
 template <int PREC>
 __device__ __forceinline__ void refill_tile_ports(const KParams& P, typename Store<PREC>::S* B, const PortTab& pt,
@@ -834,17 +853,17 @@ __device__ __forceinline__ void strip_d2q9_mom(const KParams& P, const typename 
     }
 }
 
-template <int PREC, typename IDX>
+template <int PREC, typename IDX, bool PORTS>
 __global__ void __launch_bounds__(256) k_step_d2q9_mom(const KParams P, const typename Store<PREC>::S* __restrict__ A,
                                                        typename Store<PREC>::S* __restrict__ B,
                                                        const uint32_t* __restrict__ link,
-                                                       const int* __restrict__ tiles,
-                                                       const typename Store<PREC>::T* __restrict__ gpsi_in, int gpsi_n)
+                                                       const int* __restrict__ tiles, const PortTab pt)
 {
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     int sxi, syi;
     if (!strip_of(P, tiles, gw, sxi, syi)) return;  // warp-uniform
-    strip_d2q9_mom<PREC, IDX>(P, A, B, link, sxi, syi, gpsi_in, gpsi_n);
+    strip_d2q9_mom<PREC, IDX>(P, A, B, link, sxi, syi, (const typename Store<PREC>::T*)pt.gpsi_in, pt.ng);
+    if (PORTS && pt.tab) refill_strip_ports<PREC>(P, B, pt, gw);
 }
 
 // ------------------------------------------- TMA-staged moment march (variant 8)
@@ -1248,14 +1267,23 @@ static cudaError_t launch_d2q9(lbcg_ctx* c, const void* a, void* b)
     const int threads = 256;
     const long long blocks = (warps * 32 + threads - 1) / threads;
     const uint32_t* lk = c->any_link ? c->d_link : nullptr;
-    // the ghost-psi table of the input, written by the refill launch before the step
-    const auto* gp = (const typename Store<PREC>::T*)gpsi_for(c, a);
-    const int ng = c->nghost;
-    auto go = [&](auto kern) { kern<<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl, gp, ng); };
-    if (effective_variant(c) == 6)
-        small_index(c) ? go(k_step_d2q9_mom<PREC, int>) : go(k_step_d2q9_mom<PREC, long long>);
-    else
-        small_index(c) ? go(k_step_d2q9<PREC, int>) : go(k_step_d2q9<PREC, long long>);
+    // with ports: the strips refill the ghosts of the output (and its ghost-psi table); the
+    // input's table was written by the previous step or by the refill launch before this one
+    const bool fuse = c->nghost > 0 && c->d_gstart && tl;
+    const PortTab pt{fuse ? c->d_ghost : nullptr, c->d_ghost_u, c->nghost, c->d_gstart, c->d_grow,
+                     gpsi_for(c, a), fuse ? gpsi_for(c, b) : nullptr};
+    auto go = [&](auto kern) { kern<<<(unsigned)blocks, threads, 0, c->stream>>>(P, (const S*)a, (S*)b, lk, tl, pt); };
+    if (effective_variant(c) == 6) {
+        if (small_index(c))
+            fuse ? go(k_step_d2q9_mom<PREC, int, true>) : go(k_step_d2q9_mom<PREC, int, false>);
+        else
+            fuse ? go(k_step_d2q9_mom<PREC, long long, true>) : go(k_step_d2q9_mom<PREC, long long, false>);
+    } else {
+        if (small_index(c))
+            fuse ? go(k_step_d2q9<PREC, int, true>) : go(k_step_d2q9<PREC, int, false>);
+        else
+            fuse ? go(k_step_d2q9<PREC, long long, true>) : go(k_step_d2q9<PREC, long long, false>);
+    }
     return cudaGetLastError();
 }
 
