@@ -384,6 +384,31 @@ def test_variant_switches_mid_run_ported():
     assert relmax(gr, orr) <= 1e-5 and relmax(gb, ob) <= 1e-5 and relmax(gu, ou) <= 1e-5
 
 
+# New state buffers bound mid-run (lbcg_bind_state) on ported boxes: the ghost-psi tables follow
+# the buffer pointers, the restored state has its ghosts refilled (and the new buffer's table
+# written) before the next step, so the resumed run equals the uninterrupted one bit for bit.
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_rebound_state_buffers_resume_bit_identically(lattice):
+    lb = _lb()
+    pb = (W.cross_junction(nx=96, channel_w=16, side_x=30, side_len=10, u_disp=0.01, u_cont=0.01, fill_x=20)
+          if lattice == 0 else
+          W.step_emulsifier(nx=64, ny=30, nz=10, terrace_len=20, terrace_h=4, u_in=0.01, fill_x=10))
+    for prec in (lb.LBCG_FP64, lb.LBCG_FP32_DEV):
+        ref = lb.Simulation(pb, prec)
+        ref.step(61)
+        g = lb.Simulation(pb, prec)
+        g.step(30)
+        raw = g.get_state()
+        a = torch.empty(g.state_bytes, dtype=torch.uint8, device="cuda")
+        b = torch.empty(g.state_bytes, dtype=torch.uint8, device="cuda")
+        lb._check("lbcg_bind_state", lb._lib.lbcg_bind_state(g._h, lb._vp(a.data_ptr()), lb._vp(b.data_ptr()),
+                                                            g.state_bytes))
+        g._a, g._b = a, b  # the binding keeps the new buffers alive
+        g.set_state(raw)
+        g.step(31)
+        assert np.array_equal(state(g.populations(), pb), state(ref.populations(), pb)), (pb.name, prec)
+
+
 # ------------------------------------------------------------ observables, labels
 
 def test_observables_match_oracle():
