@@ -339,10 +339,10 @@ int lbcg_kernel_time(lbcg_ctx* ctx, double* total_ms, long long* launches);
  * waits); where its conditions do not hold it runs as 7 (FP64: 6), 9 (D3Q19, regularized,
  * block_rows 3..8) variant 6 with each warp waiting per plane only for the two warps whose
  * psi rows it reads (named barriers) instead of the whole block: identical results, warps
- * up to one plane apart.  The D3Q19 moment marches (6, 7, 9) refill the port ghosts of the
- * state they write themselves (each block after its tile, from the populations it has just
- * written), so a step with ports is one launch; the other variants run the separate refill
- * kernel before each step.
+ * up to one plane apart.  The D3Q19 moment marches (6, 7, 9) and both D2Q9 strip marches
+ * refill the port ghosts of the state they write themselves (each block or warp after its
+ * tile or strip, from the populations it has just written), so a step with ports is one
+ * launch; the other variants run the separate refill kernel before each step.
  * Variants 6, 7 and 9 fall back to 5 (FP64: 2) for the BGK collision.  A context created while
  * the environment variable LBCG_TEST_PIPELINE_STALL=1 is set makes every pipeline wait of
  * variant 8 run out (failure-path test): the step then leaves the state invalid and
